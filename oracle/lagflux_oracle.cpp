@@ -1,0 +1,510 @@
+// CPU oracle for the second-order Lagrange-flux scheme of De Vuyst, Gasc,
+// Motte, Peybernes and Poncet, "Lagrange-flux schemes: reformulating
+// second-order accurate Lagrange-remap schemes for better node-based HPC
+// performance" (arXiv:1607.08710).
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+// reference that the CUDA path is checked against.  Only the test suite, the
+// smoke check and the CPU-baseline leg of the benchmark may load it.  It shares
+// no code, header, table or constant with the CUDA library, and it includes
+// nothing from it.
+//
+// Everything is FP64 (or a forward-mode dual number built on FP64), single
+// threaded, with one loop per step of the paper's Heun algorithm (Sec. 4) and
+// every face flux stored before any cell is updated.  Compiled with
+// -ffp-contract=off so that no fused multiply-add changes the rounding.
+//
+// Readings of points where the paper is silent (each is repeated in the
+// design notes):
+//   * CFL condition (Sec. 4, Heun step 1 only says "subject to some CFL
+//     condition"): dt = CFL / max_K[(|u_K|+c_K)/dx + (|v_K|+c_K)/dy] in 2D and
+//     dt = CFL / max_K[(|u_K|+c_K)/dx] in 1D, from U^n, the same dt for both
+//     stages; clipped to t_end - t when a final time is given.
+//   * MUSCL (Sec. 4, eq. "sweby" and Heun step 2): limited undivided slopes of
+//     the primitive variables (rho, u, v, p), direction by direction, with
+//     face values q_i +/- sigma_i / 2.
+//   * Upwind edge value (eq. 12 and Heun step 4): the conservative vector
+//     rebuilt from the primitive state reconstructed on the upwind side,
+//     L if u* > 0, else R.
+//   * Ghost cells: two layers; transmissive = copy of the boundary cell,
+//     periodic = wrap-around.
+//   * Derivative conventions for the dual number at non-smooth points:
+//     max/min pick the first argument on ties, the limiter is 0 (with zero
+//     derivative) when ab <= 0, and the upwind branch follows the value of u*.
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Scalar types: plain double, and a forward-mode dual number (value and one
+// tangent) used to compute exact directional derivatives of the scheme.
+// ---------------------------------------------------------------------------
+struct Dual {
+  double v, d;
+  Dual() : v(0), d(0) {}
+  Dual(double x) : v(x), d(0) {}
+  Dual(double x, double dx) : v(x), d(dx) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) {
+  double q = a.v / b.v;
+  return Dual(q, (a.d - q * b.d) / b.v);
+}
+inline Dual sqrt(Dual a) {
+  double s = std::sqrt(a.v);
+  return Dual(s, a.d / (2.0 * s));
+}
+
+inline double val(double x) { return x; }
+inline double val(const Dual& x) { return x.v; }
+inline double sq_root(double x) { return std::sqrt(x); }
+inline Dual sq_root(const Dual& x) { return sqrt(x); }
+
+template <class S> inline S abs_s(const S& a) { return val(a) < 0.0 ? S(-a) : a; }
+// First argument on ties.
+template <class S> inline S max_first(const S& a, const S& b) { return val(a) >= val(b) ? a : b; }
+template <class S> inline S min_first(const S& a, const S& b) { return val(a) <= val(b) ? a : b; }
+
+// ---------------------------------------------------------------------------
+// Configuration, mirrored field by field by the ctypes structure in oracle.py.
+// ---------------------------------------------------------------------------
+enum { LIM_MINMOD = 0, LIM_SWEBY = 1, LIM_VANLEER = 2 };
+enum { BC_TRANSMISSIVE = 0, BC_PERIODIC = 1 };
+enum { RIEMANN_MAXC = 0, RIEMANN_PER_SIDE = 1 };
+enum { ORC_OK = 0, ORC_NONPHYSICAL = 1, ORC_ARG = 2 };
+
+struct OracleConfig {
+  int32_t dim;      // 1 or 2
+  int32_t nx, ny;   // cells (ny == 1 when dim == 1)
+  int32_t limiter;  // LIM_*
+  int32_t bc;       // BC_*
+  int32_t riemann;  // RIEMANN_*
+  double dx, dy;    // cell sizes (dy unused in 1D)
+  double gamma;     // perfect-gas ratio of specific heats, in (1, 3]
+  double cfl;       // CFL number
+  double beta;      // Sweby coefficient, in [1, 2]
+};
+
+bool config_ok(const OracleConfig* c) {
+  if (!c) return false;
+  if (c->dim != 1 && c->dim != 2) return false;
+  if (c->nx < 1 || c->ny < 1) return false;
+  if (c->dim == 1 && c->ny != 1) return false;
+  if (c->limiter < 0 || c->limiter > 2) return false;
+  if (c->bc < 0 || c->bc > 1) return false;
+  if (c->riemann < 0 || c->riemann > 1) return false;
+  if (!(c->dx > 0) || (c->dim == 2 && !(c->dy > 0))) return false;
+  if (!(c->gamma > 1.0)) return false;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Eq. (1): perfect-gas EOS p = (gamma-1) rho (E - |u|^2/2), c = sqrt(gamma p / rho).
+// Primitive vector q = (rho, u, v, p); conservative U = (rho, rho u, rho v, rho E).
+// ---------------------------------------------------------------------------
+template <class S>
+void prim_from_cons(const OracleConfig& c, const S U[4], S q[4]) {
+  S rho = U[0];
+  S u = U[1] / rho;
+  S v = U[2] / rho;
+  S E = U[3] / rho;
+  q[0] = rho;
+  q[1] = u;
+  q[2] = v;
+  q[3] = (c.gamma - 1.0) * rho * (E - 0.5 * (u * u + v * v));
+}
+
+template <class S>
+void cons_from_prim(const OracleConfig& c, const S q[4], S U[4]) {
+  S rho = q[0], u = q[1], v = q[2], p = q[3];
+  U[0] = rho;
+  U[1] = rho * u;
+  U[2] = rho * v;
+  U[3] = p / (c.gamma - 1.0) + 0.5 * rho * (u * u + v * v);
+}
+
+template <class S>
+S sound_speed(const OracleConfig& c, const S& rho, const S& p) {
+  return sq_root(c.gamma * p / rho);
+}
+
+// ---------------------------------------------------------------------------
+// Eq. (sweby): phi(a,b) = (ab>0) sign(a) max(min(|a|, beta|b|), min(beta|a|, |b|)),
+// beta in [1,2]; beta = 1 is minmod (Sec. 4.2, last shock tube).  The van Leer
+// limiter (ab>0) 2ab/(a+b) is the one other classical limiter offered.
+// ---------------------------------------------------------------------------
+template <class S>
+S limiter(const OracleConfig& c, const S& a, const S& b) {
+  if (!(val(a) * val(b) > 0.0)) return S(0.0);
+  if (c.limiter == LIM_VANLEER) return 2.0 * a * b / (a + b);
+  double beta = (c.limiter == LIM_MINMOD) ? 1.0 : c.beta;
+  S aa = abs_s(a), bb = abs_s(b);
+  S m = max_first(min_first(aa, S(beta * bb)), min_first(S(beta * aa), bb));
+  return val(a) > 0.0 ? m : S(-m);
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 4.1, eqs. (13)-(14): Lagrangian HLL / acoustic interface solver.
+//   p* = (rho_R p_L + rho_L p_R)/(rho_L+rho_R)
+//        - rho_L rho_R/(rho_L+rho_R) max(c_L,c_R) (u_R - u_L)
+//   u* = (rho_L u_L + rho_R u_R)/(rho_L+rho_R)
+//        - (p_R - p_L) / ((rho_L+rho_R) max(c_L,c_R))
+// u_L, u_R are the velocities normal to the face.  The per-side variant uses
+// the impedances Z_k = rho_k c_k in the same acoustic formulas.
+// ---------------------------------------------------------------------------
+template <class S>
+void interface_solve(const OracleConfig& c, const S& rL, const S& uL, const S& pL,
+                     const S& rR, const S& uR, const S& pR, S& pstar, S& ustar) {
+  S cL = sound_speed(c, rL, pL);
+  S cR = sound_speed(c, rR, pR);
+  if (c.riemann == RIEMANN_MAXC) {
+    S a = max_first(cL, cR);
+    S rs = rL + rR;
+    pstar = (rR * pL + rL * pR) / rs - (rL * rR / rs) * a * (uR - uL);
+    ustar = (rL * uL + rR * uR) / rs - (pR - pL) / (rs * a);
+  } else {
+    S ZL = rL * cL, ZR = rR * cR;
+    S Zs = ZL + ZR;
+    pstar = (ZR * pL + ZL * pR) / Zs - (ZL * ZR / Zs) * (uR - uL);
+    ustar = (ZL * uL + ZR * uR) / Zs - (pR - pL) / Zs;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Eq. (12) with the upwinding of Sec. 4 (Heun steps 3-5): for a face with unit
+// normal nu along axis `dir` (0 = x, 1 = y), pointing from L to R,
+//   Phi = U_A (u* ) + (0, p* nu_x, p* nu_y, p* u*),
+// U_A = U(q_L) if u* > 0 else U(q_R).
+// ---------------------------------------------------------------------------
+template <class S>
+void face_flux(const OracleConfig& c, int dir, const S qL[4], const S qR[4], S F[4]) {
+  S pstar, ustar;
+  interface_solve(c, qL[0], qL[1 + dir], qL[3], qR[0], qR[1 + dir], qR[3], pstar, ustar);
+  const S* qup = (val(ustar) > 0.0) ? qL : qR;
+  S Uup[4];
+  cons_from_prim(c, qup, Uup);
+  for (int l = 0; l < 4; ++l) F[l] = Uup[l] * ustar;
+  F[1 + dir] = F[1 + dir] + pstar;
+  F[3] = F[3] + pstar * ustar;
+}
+
+// ---------------------------------------------------------------------------
+// Mesh bookkeeping: planes of nx*ny values, x fastest (index j*nx + i).
+// Ghost-extended primitive arrays have (nx+4) x (ny+4) cells in 2D and
+// (nx+4) cells in 1D, offset by G = 2.
+// ---------------------------------------------------------------------------
+const int G = 2;
+
+inline int wrap_index(int i, int n, int bc) {
+  if (bc == BC_PERIODIC) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+  }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+template <class S>
+struct Mesh {
+  const OracleConfig& c;
+  int nx, ny, gx, gy;  // interior and ghost-extended extents
+  explicit Mesh(const OracleConfig& cfg)
+      : c(cfg), nx(cfg.nx), ny(cfg.ny), gx(cfg.nx + 2 * G), gy(cfg.dim == 2 ? cfg.ny + 2 * G : 1) {}
+  size_t ncell() const { return (size_t)nx * ny; }
+  // ghost-extended index of interior-relative cell (i, j)
+  size_t gidx(int i, int j) const {
+    return (size_t)(c.dim == 2 ? j + G : 0) * gx + (i + G);
+  }
+};
+
+// Builds the ghost-extended primitive field from the conservative planes.
+template <class S>
+bool build_primitives(const Mesh<S>& m, const std::vector<S> U[4], std::vector<S> qg[4]) {
+  const OracleConfig& c = m.c;
+  for (int l = 0; l < 4; ++l) qg[l].assign((size_t)m.gx * m.gy, S(0.0));
+  bool physical = true;
+  int jlo = (c.dim == 2) ? -G : 0, jhi = (c.dim == 2) ? m.ny + G : 1;
+  for (int j = jlo; j < jhi; ++j) {
+    for (int i = -G; i < m.nx + G; ++i) {
+      // A ghost cell takes the primitive state of the interior cell it maps to.
+      int si = wrap_index(i, m.nx, c.bc);
+      int sj = (c.dim == 2) ? wrap_index(j, m.ny, c.bc) : 0;
+      size_t s = (size_t)sj * m.nx + si;
+      S Uc[4] = {U[0][s], U[1][s], U[2][s], U[3][s]};
+      S q[4];
+      prim_from_cons(c, Uc, q);
+      if (!(val(q[0]) > 0.0) || !(val(q[3]) > 0.0)) physical = false;
+      size_t g = m.gidx(i, j);
+      for (int l = 0; l < 4; ++l) qg[l][g] = q[l];
+    }
+  }
+  return physical;
+}
+
+// All face fluxes of a state (Heun steps 2-5, or 7-10).
+// Fx has (nx+1) x ny faces (face f of row j between cells f-1 and f),
+// Fy has nx x (ny+1) faces (face g of column i between cells g-1 and g).
+template <class S>
+bool all_face_fluxes(const Mesh<S>& m, const std::vector<S> U[4], std::vector<S> Fx[4],
+                     std::vector<S> Fy[4]) {
+  const OracleConfig& c = m.c;
+  std::vector<S> qg[4];
+  bool physical = build_primitives(m, U, qg);
+  auto q_at = [&](int l, int i, int j) -> S { return qg[l][m.gidx(i, j)]; };
+
+  // x-faces
+  for (int l = 0; l < 4; ++l) Fx[l].assign((size_t)(m.nx + 1) * m.ny, S(0.0));
+  for (int j = 0; j < m.ny; ++j) {
+    for (int f = 0; f <= m.nx; ++f) {
+      int iL = f - 1, iR = f;
+      S qL[4], qR[4];
+      for (int l = 0; l < 4; ++l) {
+        S sL = limiter(c, q_at(l, iL, j) - q_at(l, iL - 1, j), q_at(l, iL + 1, j) - q_at(l, iL, j));
+        S sR = limiter(c, q_at(l, iR, j) - q_at(l, iR - 1, j), q_at(l, iR + 1, j) - q_at(l, iR, j));
+        qL[l] = q_at(l, iL, j) + 0.5 * sL;
+        qR[l] = q_at(l, iR, j) - 0.5 * sR;
+      }
+      S F[4];
+      face_flux(c, 0, qL, qR, F);
+      for (int l = 0; l < 4; ++l) Fx[l][(size_t)j * (m.nx + 1) + f] = F[l];
+    }
+  }
+  // y-faces
+  if (c.dim == 2) {
+    for (int l = 0; l < 4; ++l) Fy[l].assign((size_t)m.nx * (m.ny + 1), S(0.0));
+    for (int g = 0; g <= m.ny; ++g) {
+      for (int i = 0; i < m.nx; ++i) {
+        int jL = g - 1, jR = g;
+        S qL[4], qR[4];
+        for (int l = 0; l < 4; ++l) {
+          S sL = limiter(c, q_at(l, i, jL) - q_at(l, i, jL - 1), q_at(l, i, jL + 1) - q_at(l, i, jL));
+          S sR = limiter(c, q_at(l, i, jR) - q_at(l, i, jR - 1), q_at(l, i, jR + 1) - q_at(l, i, jR));
+          qL[l] = q_at(l, i, jL) + 0.5 * sL;
+          qR[l] = q_at(l, i, jR) - 0.5 * sR;
+        }
+        S F[4];
+        face_flux(c, 1, qL, qR, F);
+        for (int l = 0; l < 4; ++l) Fy[l][(size_t)g * m.nx + i] = F[l];
+      }
+    }
+  }
+  return physical;
+}
+
+// Sum over the faces of cell K of |A| Phi_A . nu_A (outward), divided by |K|
+// (Sec. 4, semi-discrete scheme after eq. 11).  Fluxes are stored with the
+// normal pointing to +x (+y); the left (bottom) face enters with a minus sign.
+template <class S>
+S flux_balance(const Mesh<S>& m, const std::vector<S>& Fx, const std::vector<S>& Fy, int i, int j) {
+  const OracleConfig& c = m.c;
+  if (c.dim == 1) {
+    double K = c.dx, A = 1.0;
+    return (A * Fx[i + 1] - A * Fx[i]) / K;
+  }
+  double K = c.dx * c.dy, Ax = c.dy, Ay = c.dx;
+  S east = Fx[(size_t)j * (m.nx + 1) + i + 1], west = Fx[(size_t)j * (m.nx + 1) + i];
+  S north = Fy[(size_t)(j + 1) * m.nx + i], south = Fy[(size_t)j * m.nx + i];
+  return (Ax * east - Ax * west + Ay * north - Ay * south) / K;
+}
+
+// Heun step 1 under the CFL reading stated at the top of this file.
+double cfl_dt(const OracleConfig& c, const std::vector<double> U[4]) {
+  double smax = 0.0;
+  size_t n = (size_t)c.nx * c.ny;
+  for (size_t k = 0; k < n; ++k) {
+    double Uc[4] = {U[0][k], U[1][k], U[2][k], U[3][k]}, q[4];
+    prim_from_cons(c, Uc, q);
+    double a = sound_speed(c, q[0], q[3]);
+    double s = (std::fabs(q[1]) + a) / c.dx;
+    if (c.dim == 2) s += (std::fabs(q[2]) + a) / c.dy;
+    if (s > smax) smax = s;
+  }
+  return c.cfl / smax;
+}
+
+// One Heun step (Sec. 4, steps 2-11) with a given dt.
+template <class S>
+bool heun_step(const OracleConfig& c, std::vector<S> U[4], double dt) {
+  Mesh<S> m(c);
+  std::vector<S> Fxn[4], Fyn[4], Fxs[4], Fys[4], Us[4];
+  bool ok = all_face_fluxes(m, U, Fxn, Fyn);  // steps 2-5
+  for (int l = 0; l < 4; ++l) Us[l].resize(m.ncell());
+  for (int j = 0; j < m.ny; ++j)  // step 6: predicted states
+    for (int i = 0; i < m.nx; ++i) {
+      size_t k = (size_t)j * m.nx + i;
+      for (int l = 0; l < 4; ++l) Us[l][k] = U[l][k] - dt * flux_balance(m, Fxn[l], Fyn[l], i, j);
+    }
+  ok = all_face_fluxes(m, Us, Fxs, Fys) && ok;  // steps 7-10
+  for (int j = 0; j < m.ny; ++j)  // step 11: averaged fluxes
+    for (int i = 0; i < m.nx; ++i) {
+      size_t k = (size_t)j * m.nx + i;
+      for (int l = 0; l < 4; ++l) {
+        S bn = flux_balance(m, Fxn[l], Fyn[l], i, j);
+        S bs = flux_balance(m, Fxs[l], Fys[l], i, j);
+        U[l][k] = U[l][k] - dt * ((bn + bs) / 2.0);
+      }
+    }
+  // Positivity of the new state.
+  for (size_t k = 0; k < m.ncell(); ++k) {
+    S Uc[4] = {U[0][k], U[1][k], U[2][k], U[3][k]}, q[4];
+    prim_from_cons(c, Uc, q);
+    if (!(val(q[0]) > 0.0) || !(val(q[3]) > 0.0)) ok = false;
+  }
+  return ok;
+}
+
+void load_planes(const OracleConfig& c, const double* src, std::vector<double> U[4]) {
+  size_t n = (size_t)c.nx * c.ny;
+  for (int l = 0; l < 4; ++l) U[l].assign(src + l * n, src + (l + 1) * n);
+}
+void store_planes(const OracleConfig& c, const std::vector<double> U[4], double* dst) {
+  size_t n = (size_t)c.nx * c.ny;
+  for (int l = 0; l < 4; ++l) std::memcpy(dst + l * n, U[l].data(), n * sizeof(double));
+}
+
+}  // namespace
+
+// ===========================================================================
+// C entry points used through ctypes.  Arrays of 4 planes are stored plane
+// after plane (rho, rho u, rho v, rho E), each plane nx*ny values, x fastest.
+// Return ORC_OK, ORC_NONPHYSICAL (a non-positive density or pressure met) or
+// ORC_ARG (invalid configuration or argument).
+// ===========================================================================
+extern "C" {
+
+int oracle_limiter(const OracleConfig* c, int64_t n, const double* a, const double* b, double* out) {
+  if (!c || n < 0) return ORC_ARG;
+  for (int64_t k = 0; k < n; ++k) out[k] = limiter(*c, a[k], b[k]);
+  return ORC_OK;
+}
+
+// L and R are n x 3 arrays of (rho, u_normal, p).
+int oracle_interface_solve(const OracleConfig* c, int64_t n, const double* L, const double* R,
+                           double* pstar, double* ustar) {
+  if (!c || n < 0) return ORC_ARG;
+  for (int64_t k = 0; k < n; ++k)
+    interface_solve(*c, L[3 * k], L[3 * k + 1], L[3 * k + 2], R[3 * k], R[3 * k + 1], R[3 * k + 2],
+                    pstar[k], ustar[k]);
+  return ORC_OK;
+}
+
+// qL, qR, F are n x 4 arrays; q = (rho, u, v, p).
+int oracle_face_flux(const OracleConfig* c, int dir, int64_t n, const double* qL, const double* qR,
+                     double* F) {
+  if (!c || n < 0 || (dir != 0 && dir != 1)) return ORC_ARG;
+  for (int64_t k = 0; k < n; ++k) face_flux(*c, dir, qL + 4 * k, qR + 4 * k, F + 4 * k);
+  return ORC_OK;
+}
+
+int oracle_prim_to_cons(const OracleConfig* c, const double* q, double* U) {
+  if (!config_ok(c)) return ORC_ARG;
+  size_t n = (size_t)c->nx * c->ny;
+  for (size_t k = 0; k < n; ++k) {
+    double qc[4] = {q[k], q[n + k], q[2 * n + k], q[3 * n + k]}, Uc[4];
+    cons_from_prim(*c, qc, Uc);
+    for (int l = 0; l < 4; ++l) U[l * n + k] = Uc[l];
+  }
+  return ORC_OK;
+}
+
+int oracle_cons_to_prim(const OracleConfig* c, const double* U, double* q) {
+  if (!config_ok(c)) return ORC_ARG;
+  size_t n = (size_t)c->nx * c->ny;
+  for (size_t k = 0; k < n; ++k) {
+    double Uc[4] = {U[k], U[n + k], U[2 * n + k], U[3 * n + k]}, qc[4];
+    prim_from_cons(*c, Uc, qc);
+    for (int l = 0; l < 4; ++l) q[l * n + k] = qc[l];
+  }
+  return ORC_OK;
+}
+
+int oracle_dt(const OracleConfig* c, const double* Uin, double* dt) {
+  if (!config_ok(c) || !Uin || !dt) return ORC_ARG;
+  std::vector<double> U[4];
+  load_planes(*c, Uin, U);
+  *dt = cfl_dt(*c, U);
+  return ORC_OK;
+}
+
+// L(U) = -(1/|K|) sum_A |A| Phi_A, the right-hand side of the semi-discrete
+// scheme after eq. (11).
+int oracle_residual(const OracleConfig* c, const double* Uin, double* LU) {
+  if (!config_ok(c) || !Uin || !LU) return ORC_ARG;
+  std::vector<double> U[4], Fx[4], Fy[4];
+  load_planes(*c, Uin, U);
+  Mesh<double> m(*c);
+  bool ok = all_face_fluxes(m, U, Fx, Fy);
+  size_t n = m.ncell();
+  for (int j = 0; j < m.ny; ++j)
+    for (int i = 0; i < m.nx; ++i)
+      for (int l = 0; l < 4; ++l)
+        LU[l * n + (size_t)j * m.nx + i] = -flux_balance(m, Fx[l], Fy[l], i, j);
+  return ok ? ORC_OK : ORC_NONPHYSICAL;
+}
+
+// Runs up to max_steps Heun steps.  If dts_in is given, step n uses dts_in[n]
+// (a frozen dt sequence); otherwise dt comes from the CFL condition and is
+// clipped so that t never passes t_end (t_end <= 0: no final time).  The run
+// stops early once t reaches t_end.  dts_out (nullable) receives the dt used
+// by each step.
+int oracle_run(const OracleConfig* c, double* Uio, int32_t max_steps, double t0, double t_end,
+               const double* dts_in, double* dts_out, int32_t* steps_done, double* t_out) {
+  if (!config_ok(c) || !Uio || max_steps < 0) return ORC_ARG;
+  std::vector<double> U[4];
+  load_planes(*c, Uio, U);
+  double t = t0;
+  int n = 0;
+  int status = ORC_OK;
+  for (; n < max_steps; ++n) {
+    if (t_end > 0.0 && !dts_in && t >= t_end) break;
+    double dt = dts_in ? dts_in[n] : cfl_dt(*c, U);
+    if (!dts_in && t_end > 0.0 && t + dt > t_end) dt = t_end - t;
+    if (dts_out) dts_out[n] = dt;
+    if (!heun_step(*c, U, dt)) {
+      status = ORC_NONPHYSICAL;
+      ++n;
+      t += dt;
+      break;
+    }
+    t += dt;
+  }
+  store_planes(*c, U, Uio);
+  if (steps_done) *steps_done = n;
+  if (t_out) *t_out = t;
+  return status;
+}
+
+// Forward-mode directional derivative of nsteps Heun steps with the frozen
+// dt sequence dts.  q0 and dq0 are the initial primitive planes (rho, u, v, p)
+// and their tangent; U_out and dU_out receive the final conservative planes
+// and their tangent.
+int oracle_run_tangent(const OracleConfig* c, const double* q0, const double* dq0, int32_t nsteps,
+                       const double* dts, double* U_out, double* dU_out) {
+  if (!config_ok(c) || !q0 || !dq0 || !dts || nsteps < 0) return ORC_ARG;
+  size_t n = (size_t)c->nx * c->ny;
+  std::vector<Dual> U[4];
+  for (int l = 0; l < 4; ++l) U[l].resize(n);
+  for (size_t k = 0; k < n; ++k) {
+    Dual qc[4], Uc[4];
+    for (int l = 0; l < 4; ++l) qc[l] = Dual(q0[l * n + k], dq0[l * n + k]);
+    cons_from_prim(*c, qc, Uc);
+    for (int l = 0; l < 4; ++l) U[l][k] = Uc[l];
+  }
+  int status = ORC_OK;
+  for (int s = 0; s < nsteps; ++s)
+    if (!heun_step(*c, U, dts[s])) status = ORC_NONPHYSICAL;
+  for (int l = 0; l < 4; ++l)
+    for (size_t k = 0; k < n; ++k) {
+      U_out[l * n + k] = U[l][k].v;
+      dU_out[l * n + k] = U[l][k].d;
+    }
+  return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,166 @@
+"""Seeded synthetic initial conditions.
+
+This module only draws and lays out primitive fields (rho, u, v, p) on cell
+centres; it holds none of the scheme's arithmetic (no equation of state, no
+flux), so that the CUDA path and the CPU oracle can both start from exactly the
+same input.  Every array is float64 with shape (ny, nx), x fastest; 1D
+problems have ny == 1.
+
+Workloads:
+  * shock tubes of Sec. 4.2 (Sod, two-rarefaction, sonic rarefaction,
+    shock-shock) on [0, 1] with the interface at x = 0.5;
+  * seeded four-quadrant 2D Riemann problems on [0, 1]^2;
+  * a smooth density wave rho = 1 + 0.2 sin(2 pi (x + y)), u = v = 0.5, p = 1,
+    whose exact solution is a translation;
+  * a seeded Kelvin-Helmholtz shear layer;
+  * seeded mesh sizes for batches of independent problems.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+# (rho, u, p) left and right states of the shock tubes of Sec. 4.2.
+SHOCK_TUBES = {
+    "sod": ((1.0, 0.0, 1.0), (0.125, 0.0, 0.1)),
+    "two_rarefaction": ((1.0, -2.0, 0.4), (1.0, 2.0, 0.4)),
+    "sonic_rarefaction": ((5.0, 0.0, 5.0), (0.125, 0.0, 0.1)),
+    "shock_shock": ((1.0, 5.0, 1.0), (1.0, -5.0, 0.01)),
+}
+
+
+@dataclass
+class Primitive:
+    """Primitive fields on cell centres, each of shape (ny, nx)."""
+
+    rho: np.ndarray
+    u: np.ndarray
+    v: np.ndarray
+    p: np.ndarray
+
+    def stack(self) -> np.ndarray:
+        return np.stack([self.rho, self.u, self.v, self.p]).astype(np.float64)
+
+    @property
+    def shape(self):
+        return self.rho.shape
+
+
+def cell_centres(n: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+    return lo + (np.arange(n, dtype=np.float64) + 0.5) * ((hi - lo) / n)
+
+
+def shock_tube(nx: int, left, right, x0: float = 0.5) -> Primitive:
+    """1D Riemann problem on [0, 1]: left state for x < x0, right state otherwise."""
+    x = cell_centres(nx)
+    is_left = x < x0
+    rho = np.where(is_left, left[0], right[0])[None, :]
+    u = np.where(is_left, left[1], right[1])[None, :]
+    p = np.where(is_left, left[2], right[2])[None, :]
+    return Primitive(rho.copy(), u.copy(), np.zeros_like(rho), p.copy())
+
+
+def named_shock_tube(name: str, nx: int) -> Primitive:
+    left, right = SHOCK_TUBES[name]
+    return shock_tube(nx, left, right)
+
+
+def quadrant_states(seed: int) -> np.ndarray:
+    """Four constant states, rows in the order NE, NW, SW, SE, columns (rho, u, v, p).
+
+    rho ~ U[0.5, 1.5], u, v ~ U[-0.75, 0.75], p ~ U[0.1, 1.0], drawn quadrant by
+    quadrant in the order rho, u, v, p from numpy's default generator.
+    """
+    rng = np.random.default_rng(seed)
+    out = np.empty((4, 4))
+    for q in range(4):
+        out[q, 0] = rng.uniform(0.5, 1.5)
+        out[q, 1] = rng.uniform(-0.75, 0.75)
+        out[q, 2] = rng.uniform(-0.75, 0.75)
+        out[q, 3] = rng.uniform(0.1, 1.0)
+    return out
+
+
+def quadrant(nx: int, ny: int | None = None, seed: int = 0) -> Primitive:
+    """Four-quadrant 2D Riemann problem on [0, 1]^2, split at x = y = 0.5."""
+    ny = nx if ny is None else ny
+    st = quadrant_states(seed)
+    x = cell_centres(nx)[None, :]
+    y = cell_centres(ny)[:, None]
+    east, north = x >= 0.5, y >= 0.5
+    idx = np.where(north & east, 0, np.where(north, 1, np.where(east, 3, 2)))
+    return Primitive(st[idx, 0], st[idx, 1], st[idx, 2], st[idx, 3])
+
+
+def smooth_wave(nx: int, ny: int | None = None, t: float = 0.0) -> Primitive:
+    """rho = 1 + 0.2 sin(2 pi (x + y - t)), u = v = 0.5, p = 1 (periodic square).
+
+    With u = v = 0.5 the exact solution at time t is the initial profile moved
+    by (t/2, t/2), i.e. the phase x + y - t.
+    """
+    ny = nx if ny is None else ny
+    x = cell_centres(nx)[None, :]
+    y = cell_centres(ny)[:, None]
+    rho = 1.0 + 0.2 * np.sin(2.0 * math.pi * (x + y - t))
+    one = np.ones((ny, nx))
+    return Primitive(rho, 0.5 * one, 0.5 * one, one.copy())
+
+
+def smooth_wave_1d(nx: int, t: float = 0.0) -> Primitive:
+    """rho = 1 + 0.2 sin(2 pi (x - t)), u = 1, p = 1 on the periodic unit interval."""
+    x = cell_centres(nx)[None, :]
+    rho = 1.0 + 0.2 * np.sin(2.0 * math.pi * (x - t))
+    one = np.ones((1, nx))
+    return Primitive(rho, one.copy(), np.zeros((1, nx)), one.copy())
+
+
+def kelvin_helmholtz(nx: int, ny: int | None = None, seed: int = 0, amplitude: float = 0.01,
+                     modes: int = 8) -> Primitive:
+    """Shear layer: rho = 2, u = +0.5 inside |y - 0.5| < 0.25; rho = 1, u = -0.5 outside; p = 2.5.
+
+    v = amplitude * S(x) / max|S| with S(x) = sum_{k=1..modes} a_k sin(2 pi k x + phi_k),
+    a_k ~ U[0, 1], phi_k ~ U[0, 2 pi) drawn (all a_k, then all phi_k) from
+    numpy's default generator.
+    """
+    ny = nx if ny is None else ny
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0.0, 1.0, modes)
+    phi = rng.uniform(0.0, 2.0 * math.pi, modes)
+    x = cell_centres(nx)
+    y = cell_centres(ny)[:, None]
+    k = np.arange(1, modes + 1)[:, None]
+    S = (a[:, None] * np.sin(2.0 * math.pi * k * x[None, :] + phi[:, None])).sum(axis=0)
+    vrow = amplitude * S / np.max(np.abs(S))
+    inside = np.abs(y - 0.5) < 0.25
+    rho = np.where(inside, 2.0, 1.0) * np.ones((1, nx))
+    u = np.where(inside, 0.5, -0.5) * np.ones((1, nx))
+    v = np.broadcast_to(vrow[None, :], (ny, nx)).copy()
+    p = np.full((ny, nx), 2.5)
+    return Primitive(rho, u, v, p)
+
+
+def smooth_perturbation(nx: int, ny: int | None = None, seed: int = 0, modes: int = 4) -> np.ndarray:
+    """Seeded smooth periodic field of unit max amplitude (a sum of low Fourier modes)."""
+    ny = nx if ny is None else ny
+    rng = np.random.default_rng(seed)
+    x = cell_centres(nx)[None, :]
+    y = cell_centres(ny)[:, None]
+    f = np.zeros((ny, nx))
+    for _ in range(modes):
+        kx, ky = rng.integers(1, 4, size=2)
+        ph = rng.uniform(0.0, 2.0 * math.pi)
+        amp = rng.uniform(0.5, 1.0)
+        f += amp * np.sin(2.0 * math.pi * (kx * x + ky * y) + ph)
+    return f / np.max(np.abs(f))
+
+
+def batched_sizes(nprob: int, seed: int = 0, lo: int = 64, hi: int = 1024) -> np.ndarray:
+    """(nprob, 2) array of (nx, ny), each side round(exp(U[ln lo, ln hi])), drawn nx then ny."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((nprob, 2), dtype=np.int64)
+    for k in range(nprob):
+        out[k, 0] = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+        out[k, 1] = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+    return out
