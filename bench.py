@@ -1,0 +1,408 @@
+"""Throughput benchmark of the Lagrange-flux hot path on one GB300 (or N replicas).
+
+A "step" is one full Heun/RK2 time step (Sec. 4, steps 1-11: CFL dt from the
+device-side wave-speed maximum, fused predictor, fused corrector) over the
+whole mesh.  Default workload: the 8192 x 8192 periodic Kelvin-Helmholtz
+shear layer (gamma 1.4, van Leer MUSCL, CFL 0.45) in FP32, the mesh of the
+FP32-vs-FP64 precision study.  The state (1.07 GB in FP32) is far larger than
+the 129 MB L2, so no L2 flush is needed between steps.
+
+Printed: one JSON line (rank 0) with cell-updates/s, the per-kernel HBM
+roofline of the dominant kernel (timed live with CUDA events on the solver's
+stream), the FP64 path on the same workload, the FP32-vs-FP64 error after the
+FP64 steps, an end-to-end number through the host-buffer API, SM clocks
+sampled during the timed region, and the CPU oracle timed on a bounded sample
+(the CPU baseline).  `--impl reference` times the CPU oracle alone.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s"
+BYTES_PER_CELL = {  # algorithmic bytes per cell per launch: words read + written x word size
+    ("stage0", "fp32"): 8 * 4, ("stage1", "fp32"): 12 * 4,
+    ("stage0", "fp64"): 8 * 8, ("stage1", "fp64"): 12 * 8,
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=8192)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--cpu-sample-size", type=int, default=1024)
+    ap.add_argument("--cpu-sample-steps", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(args):
+    return {"workload": f"periodic Kelvin-Helmholtz shear layer {args.size}x{args.size}",
+            "nx": args.size, "ny": args.size, "gamma": 1.4, "limiter": "van Leer", "cfl": 0.45,
+            "bc": "periodic", "riemann": "eqs. 13-14, a = max(c_L, c_R)", "seed": 0,
+            "l2_policy": "inputs larger than L2 (state %.2f GB vs 129 MB L2), no flush" %
+                         (4 * args.size * args.size * (4 if args.precision == "fp32" else 8) / 1e9)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only: no data-path collective)
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group("gloo")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+
+        t = torch.tensor([x], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="lf_clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "50"], stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.1)
+        self.proc.terminate()
+        self.proc.wait()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            if self.uuid and self.uuid not in f[1]:
+                continue
+            rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[4]) for r in rows if r[4].replace(".", "").isdigit()), default=None)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1607_08710_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, cells: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
+    to `cells`; None when absent or taken on different kernel sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        e = d["kernels"][kernel]
+        if d.get("source_hash") != kernel_source_hash():
+            return None
+        return e["dram_bytes_per_launch"] * cells / e["cells"]
+    except (KeyError, ValueError, ZeroDivisionError):
+        return None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(args):
+    """The CPU oracle as it stands (single thread), on a bounded sample of the
+    same workload: the same shear-layer generator on a smaller periodic mesh."""
+    from oracle import oracle as O
+    from paper_1607_08710_gb300 import inputs
+
+    n, steps = args.cpu_sample_size, args.cpu_sample_steps
+    oc = O.OracleConfig(nx=n, ny=n, limiter="vanleer", bc="periodic", cfl=0.45)
+    U0 = O.prim_to_cons(oc, inputs.kelvin_helmholtz(n, n, seed=0).stack())
+    O.run(oc, U0, 1)  # warm the library
+    t0 = time.perf_counter()
+    r = O.run(oc, U0, steps)
+    el = time.perf_counter() - t0
+    return {"value": n * n * r.steps / el, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle, periodic Kelvin-Helmholtz {n}x{n}, {r.steps} steps ({el:.1f} s), single thread",
+            "seconds": el}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1607_08710_gb300 import inputs
+
+    n = args.cpu_sample_size
+    oc = O.OracleConfig(nx=n, ny=n, limiter="vanleer", bc="periodic", cfl=0.45)
+    U = O.prim_to_cons(oc, inputs.kelvin_helmholtz(n, n, seed=0).stack())
+    for _ in range(args.warmup):
+        U = O.run(oc, U, 1).U
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U = O.run(oc, U, 1).U
+    el = time.perf_counter() - t0
+    v = n * n * args.steps / el
+    cfg = workload_config(args)
+    sample = f"FP64 oracle, each step one Heun step of the same shear layer on {n}x{n} cells, single thread"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, dist):
+    import torch
+
+    from paper_1607_08710_gb300 import inputs
+    from paper_1607_08710_gb300.lagflux import Config, LagrangeFlux
+
+    torch.cuda.set_device(dist.local_rank)
+    dev = torch.device("cuda", dist.local_rank)
+    n = args.size
+    cells = n * n
+    prec = args.precision
+    tdt = torch.float32 if prec == "fp32" else torch.float64
+    prim = inputs.kelvin_helmholtz(n, n, seed=0).stack()
+    kw = dict(nx=n, ny=n, limiter="vanleer", bc="periodic", cfl=0.45, device=dist.local_rank)
+
+    solver = LagrangeFlux(Config(precision=prec, **kw))
+    q = torch.from_numpy(prim).to(dev, tdt)
+    solver.set_primitive(q[0], q[1], q[2], q[3])
+    del q
+    for _ in range(args.warmup):
+        solver.step()
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    start.record()
+    for _ in range(args.steps):
+        solver.step()
+    stop.record()
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    t_local = start.elapsed_time(stop) / 1e3
+    solver.sync()  # raises on a device-side error flag
+    t = dist.max(t_local)
+    value = dist.world * cells * args.steps / t
+
+    # per-kernel device time (separate pass, so the tracing events do not touch the timed number)
+    solver.profile(True)
+    for _ in range(args.profile_steps):
+        solver.step()
+    (ms0, ms1), (n0, n1) = solver.profile_read()
+    solver.profile(False)
+    kernels = {}
+    for name, ms, cnt in (("stage0", ms0, n0), ("stage1", ms1, n1)):
+        avg = ms / cnt / 1e3
+        b = BYTES_PER_CELL[(name, prec)] * cells
+        kernels[name] = {"avg_ms": avg * 1e3, "launches": cnt, "algorithmic_bytes": b, "gbs": b / avg / 1e9}
+    dom = max(kernels, key=lambda k: kernels[k]["avg_ms"])
+    peak, peak_kind = peaks()
+    kname = {"stage0": "stage2d_kernel<%s, VANLEER, predictor>", "stage1": "stage2d_kernel<%s, VANLEER, corrector>"}
+    kname = {k: v % ("float" if prec == "fp32" else "double") for k, v in kname.items()}
+    traffic = measured_traffic(kname[dom], cells)
+    roofline = {"bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": kernels[dom]["gbs"] / peak, "traffic": traffic, "kernel": kname[dom],
+                "peak_kind": f"{peak_kind} copy bandwidth",
+                "step_frac": (sum(BYTES_PER_CELL[(k, prec)] for k in ("stage0", "stage1")) * cells * args.steps / t_local
+                              / 1e9) / peak}
+
+    out = {}
+    # FP64 path on the same workload, and the FP32-vs-FP64 error after those steps
+    if prec == "fp32" and not args.no_fp64 and dist.rank == 0:
+        s64 = LagrangeFlux(Config(precision="fp64", **kw))
+        q = torch.from_numpy(prim).to(dev, torch.float64)
+        s64.set_primitive(q[0], q[1], q[2], q[3])
+        s64.step()  # warm-up
+        s64.set_primitive(q[0], q[1], q[2], q[3])
+        del q
+        dts = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.fp64_steps):
+            s64.step()
+        e1.record()
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        s64.profile(True)
+        s64.step()
+        (m0, m1), _ = s64.profile_read()
+        s64.profile(False)
+        # replay the FP64 dt sequence in FP32 from the same initial state
+        s64.set_primitive(*torch.from_numpy(prim).to(dev, torch.float64))
+        for _ in range(args.fp64_steps):
+            dts.append(s64.step(return_dt=True))
+        ref = torch.empty((4, n, n), dtype=torch.float64, device=dev)
+        s64.get_state(ref)
+        s64.close()
+        s32 = LagrangeFlux(Config(precision="fp32", **kw))
+        s32.set_primitive(*torch.from_numpy(prim).to(dev, torch.float32))
+        for dt in dts:
+            s32.step_fixed(dt)
+        got = torch.empty((4, n, n), dtype=torch.float32, device=dev)
+        s32.get_state(got)
+        s32.close()
+        l1 = [float((got[l].double() - ref[l]).abs().sum() / ref[l].abs().sum()) for l in range(4)]
+        del ref, got
+        v64 = cells * args.fp64_steps / t64
+        out["fp64"] = {"value": v64, "unit": METRIC, "steps": args.fp64_steps, "ms_per_step": 1e3 * t64 / args.fp64_steps,
+                       "stage_ms": [m0, m1]}
+        out["fp32_over_fp64"] = value / dist.world / v64
+        out["l1_error"] = {"fp32_vs_fp64_relative_l1": dict(zip(["rho", "rhou", "rhov", "rhoE"], l1)),
+                           "after_steps": args.fp64_steps}
+        torch.cuda.empty_cache()
+
+    # end to end through the host-buffer API: pinned host state in, one step, state out
+    if not args.no_e2e:
+        hin = torch.from_numpy(prim).to(dev, tdt)
+        solver.set_primitive(hin[0], hin[1], hin[2], hin[3])
+        U = torch.empty((4, n, n), dtype=tdt, device=dev)
+        solver.get_state(U)
+        h_in = U.cpu().pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        del U, hin
+        solver.set_state(h_in[0], h_in[1], h_in[2], h_in[3])
+        solver.step()
+        solver.get_state(h_out)
+        torch.cuda.synchronize()
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            solver.set_state(h_out[0], h_out[1], h_out[2], h_out[3])
+            solver.step()
+            solver.get_state(h_out)
+        torch.cuda.synchronize()
+        te = dist.max(time.perf_counter() - t0)
+        nbytes = h_in.numel() * h_in.element_size()
+        out["e2e"] = {"value": dist.world * cells * args.e2e_steps / te, "unit": METRIC,
+                      "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                      "how": "per step: lf_set_state from pinned host planes, lf_step, lf_get_state to pinned host"}
+        del h_in, h_out
+    solver.close()
+
+    if dist.rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+        "config": dict(workload_config(args), parallelism=f"replicas x{dist.world}" if dist.world > 1 else "single GPU"),
+        "roofline": roofline, "kernels": kernels, "gpu_launches": 4 * args.steps, "clocks": clk,
+    }
+    line.update(out)
+    if not args.no_cpu_baseline and dist.world == 1:
+        line["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        else:
+            run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

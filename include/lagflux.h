@@ -1,0 +1,160 @@
+/*
+ * lagflux.h -- C ABI of the GB300 (sm_103a) Lagrange-flux solver.
+ *
+ * The library advances the 1D/2D compressible Euler equations with a
+ * perfect-gas equation of state (arXiv:1607.08710, Sec. 3, eq. 1) by the
+ * second-order Lagrange-flux scheme of Sec. 4: MUSCL reconstruction of the
+ * primitive variables with a limited slope (eq. "sweby"), the Lagrangian
+ * HLL / acoustic interface solver (Sec. 4.1, eqs. 13-14), the upwind
+ * Lagrange flux (eq. 12) and the two-stage Heun time integrator (Sec. 4,
+ * steps 1-11) under a CFL time step.
+ *
+ * Conventions shared by every entry point:
+ *   - Mesh: a uniform Cartesian mesh of nx x ny cells on
+ *     [xmin, xmax] x [ymin, ymax] (ny == 1 and the y bounds unused in 1D).
+ *   - Fields are passed as separate planes of nx*ny elements, x fastest
+ *     (element (i, j) at index j*nx + i), of the configured precision:
+ *     double for LF_FP64, float for LF_FP32.  The conservative planes are
+ *     (rho, rho u, rho v, rho E); the primitive planes (rho, u, v, p).
+ *   - Ownership: the caller owns every buffer it passes and keeps it; the
+ *     library copies in and out and never retains a caller pointer.  The
+ *     context owns its device state, scratch and scalars.
+ *   - `on_device` = 1: the pointers are device pointers (e.g. the data_ptr of
+ *     a contiguous CUDA tensor) readable on the context's device; 0: host
+ *     pointers.  Host transfers complete before the call returns.
+ *   - Streams: all device work is enqueued on the stream given to lf_init
+ *     (NULL = the legacy default stream).  Calls return once the work is
+ *     enqueued, except where they must return a host value (dt_out,
+ *     steps_done, t_out, sums) or touch host memory; those synchronise the
+ *     stream first.
+ *   - Errors: no call aborts or throws.  Invalid arguments return
+ *     LF_ERR_ARG and change nothing.  A CUDA failure returns LF_ERR_CUDA.
+ *     Device kernels never trap: a non-positive density or pressure, or a
+ *     non-finite wave speed, sets a sticky flag in the context; the next
+ *     synchronising call returns LF_ERR_NONPHYSICAL and the time loop stops
+ *     advancing (dt becomes 0).  lf_last_error describes the last failure.
+ *   - Thread safety: one context must not be used from two host threads at
+ *     once; distinct contexts are independent.
+ */
+#ifndef LAGFLUX_H
+#define LAGFLUX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lf_status {
+  LF_OK = 0,
+  LF_ERR_ARG = 1,         /* invalid argument or configuration */
+  LF_ERR_CUDA = 2,        /* a CUDA runtime call or launch failed */
+  LF_ERR_OOM = 3,         /* device memory allocation failed */
+  LF_ERR_NONPHYSICAL = 4, /* non-positive rho or p, or non-finite wave speed */
+  LF_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  LF_ERR_STATE = 6        /* call out of order (e.g. step before a state was set) */
+} lf_status;
+
+/* Slope limiters: Sweby's phi(a,b) of Sec. 4 (eq. "sweby") with beta in
+ * [1, 2]; beta = 1 is minmod (Sec. 4.2, last tube).  Van Leer's
+ * (ab>0) 2ab/(a+b) is the one limiter offered beyond the paper's. */
+enum { LF_LIMITER_MINMOD = 0, LF_LIMITER_SWEBY = 1, LF_LIMITER_VANLEER = 2 };
+/* Boundary conditions: transmissive (two ghost layers copying the boundary
+ * cell) or periodic (wrap-around). */
+enum { LF_BC_TRANSMISSIVE = 0, LF_BC_PERIODIC = 1 };
+/* Arithmetic precision of the state, fluxes and updates.  In LF_FP32 the
+ * time, dt, the dt reduction's input and the conservation sums stay FP64. */
+enum { LF_FP64 = 0, LF_FP32 = 1 };
+/* Interface solver: eqs. (13)-(14) with a = max(c_L, c_R) (default), or the
+ * acoustic solver with per-side impedances Z_k = rho_k c_k. */
+enum { LF_RIEMANN_MAXC = 0, LF_RIEMANN_PER_SIDE = 1 };
+
+typedef struct lf_config {
+  int32_t dim;       /* 1 or 2 */
+  int32_t nx, ny;    /* cells per direction; ny == 1 when dim == 1 */
+  int32_t limiter;   /* LF_LIMITER_* */
+  int32_t bc;        /* LF_BC_* */
+  int32_t precision; /* LF_FP64 or LF_FP32 */
+  int32_t riemann;   /* LF_RIEMANN_* */
+  int32_t device;    /* CUDA device ordinal */
+  double xmin, xmax; /* domain in x */
+  double ymin, ymax; /* domain in y (ignored in 1D) */
+  double gamma;      /* ratio of specific heats, 1 < gamma <= 3 (Sec. 3) */
+  double cfl;        /* CFL number, 0 < cfl <= 1 */
+  double beta;       /* Sweby coefficient, 1 <= beta <= 2 (LF_LIMITER_SWEBY) */
+} lf_config;
+
+typedef struct lf_ctx lf_ctx;
+
+/* Creates a solver for one mesh.  `stream` is a cudaStream_t (NULL: default
+ * stream).  Allocates the device state (4 planes), one intermediate Heun
+ * state (4 planes) and a few scalars.  *out is set only on LF_OK. */
+lf_status lf_init(const lf_config* cfg, void* stream, lf_ctx** out);
+
+/* Frees everything the context owns.  NULL is ignored. */
+void lf_destroy(lf_ctx* ctx);
+
+/* Copies in a conservative state (rho, rho u, rho v, rho E); in 1D rhov may
+ * be NULL (taken as 0).  Resets t to 0 and the step count to 0 and computes
+ * the wave-speed maximum for the first dt (Sec. 4, Heun step 1). */
+lf_status lf_set_state(lf_ctx* ctx, const void* rho, const void* rhou, const void* rhov,
+                       const void* rhoE, int on_device);
+
+/* As lf_set_state from primitive planes (rho, u, v, p); the conversion uses
+ * the perfect-gas EOS of eq. (1) and runs on the device. */
+lf_status lf_set_primitive(lf_ctx* ctx, const void* rho, const void* u, const void* v,
+                           const void* p, int on_device);
+
+/* Copies out the current conservative state; rhov may be NULL in 1D. */
+lf_status lf_get_state(lf_ctx* ctx, void* rho, void* rhou, void* rhov, void* rhoE,
+                       int on_device);
+
+/* Copies out the current primitive state (rho, u, v, p) via eq. (1). */
+lf_status lf_get_primitive(lf_ctx* ctx, void* rho, void* u, void* v, void* p, int on_device);
+
+/* One Heun step (Sec. 4, steps 1-11) with the CFL time step
+ * dt = cfl / max_K[(|u|+c)/dx + (|v|+c)/dy]  (1D: cfl / max_K[(|u|+c)/dx]).
+ * dt_out (nullable) receives the dt used; passing it synchronises. */
+lf_status lf_step(lf_ctx* ctx, double* dt_out);
+
+/* One Heun step with a caller-chosen dt > 0 (e.g. to replay a recorded dt
+ * sequence).  Does not synchronise. */
+lf_status lf_step_fixed(lf_ctx* ctx, double dt);
+
+/* Advances until t reaches t_end (t_end <= 0: no final time) or max_steps
+ * steps are done.  The last dt is clipped so that t lands on t_end.  dt stays
+ * on the device; the host only polls t between batches of steps.
+ * steps_done and t_out are nullable; the call synchronises. */
+lf_status lf_run(lf_ctx* ctx, double t_end, int32_t max_steps, int32_t* steps_done, double* t_out);
+
+/* Current time and completed step count (synchronises). */
+lf_status lf_get_time(lf_ctx* ctx, double* t, int64_t* steps);
+
+/* Compensated (Neumaier) FP64 sums of the four conservative fields over all
+ * cells, in a fixed (deterministic) reduction order.  out[4]; synchronises. */
+lf_status lf_conservation_sums(lf_ctx* ctx, double out[4]);
+
+/* Waits for the context's stream and reports any device-side error flag. */
+lf_status lf_sync(lf_ctx* ctx);
+
+/* Stage tracing.  While enabled, every predictor (stage 0) and corrector
+ * (stage 1) kernel launch is bracketed by CUDA events recorded on the
+ * context's stream.  lf_profile_read synchronises and returns, per stage,
+ * the summed device time in milliseconds and the number of launches timed
+ * since tracing was (re-)enabled.  Enabling resets the accumulators.  Timing
+ * adds two event records per launch; leave it off for throughput runs. */
+lf_status lf_profile_enable(lf_ctx* ctx, int enable);
+lf_status lf_profile_read(lf_ctx* ctx, double ms[2], int64_t launches[2]);
+
+/* Human-readable name of a status code (static storage). */
+const char* lf_status_string(lf_status s);
+
+/* Description of the last failure on this context (static per context;
+ * valid until the next call on it).  NULL ctx: the last lf_init failure. */
+const char* lf_last_error(const lf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LAGFLUX_H */

@@ -1,0 +1,513 @@
+// C ABI of liblagflux (declared in include/lagflux.h): context management,
+// state transfer, and the Heun time loop of arXiv:1607.08710, Sec. 4, driven
+// entirely by device-side scalars.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../../include/lagflux.h"
+#include "lf_internal.h"
+
+struct lf_ctx {
+  lf_config cfg;
+  lf::MeshDesc mesh;
+  cudaStream_t stream = nullptr;
+  size_t elem = 8;            // bytes per element
+  void* U = nullptr;          // current state, 4 pitched planes
+  void* Ustar = nullptr;      // Heun predictor state, 4 pitched planes
+  void* staging = nullptr;    // dense 4 planes for host primitive transfers (lazy)
+  lf::Scalars* sc = nullptr;  // device scalars
+  lf::Scalars* hsc = nullptr; // pinned host mirror for read-back
+  double* partials = nullptr; // conservation-sum partials
+  double* dsums = nullptr;    // 4 device doubles
+  bool has_state = false;
+  // stage tracing: event pairs recorded around each stage launch
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_stage;   // stage of each recorded pair
+  size_t ev_used = 0;          // pairs recorded
+  char last_error[512] = {0};
+};
+
+namespace {
+
+char g_init_error[512] = "";
+
+void set_err(lf_ctx* c, const char* fmt, ...) {
+  char* dst = c ? c->last_error : g_init_error;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+}
+
+// Makes the context's device current for the duration of a call and puts
+// the caller's device back afterwards.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+lf_status cuda_fail(lf_ctx* c, cudaError_t e, const char* what) {
+  set_err(c, "%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? LF_ERR_OOM : LF_ERR_CUDA;
+}
+
+#define LF_CUDA(ctx, call)                                  \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+const char* validate(const lf_config* c) {
+  if (!c) return "config is NULL";
+  if (c->dim != 1 && c->dim != 2) return "dim must be 1 or 2";
+  if (c->nx < 1 || c->ny < 1) return "nx and ny must be >= 1";
+  if (c->dim == 1 && c->ny != 1) return "ny must be 1 when dim == 1";
+  if ((long long)c->nx * c->ny > (1LL << 31)) return "mesh larger than 2^31 cells";
+  if (c->limiter < 0 || c->limiter > 2) return "unknown limiter";
+  if (c->bc < 0 || c->bc > 1) return "unknown boundary condition";
+  if (c->precision != LF_FP64 && c->precision != LF_FP32) return "unknown precision";
+  if (c->riemann < 0 || c->riemann > 1) return "unknown interface solver";
+  if (c->device < 0) return "device must be >= 0";
+  if (!(c->xmax > c->xmin) || !std::isfinite(c->xmax - c->xmin)) return "need xmin < xmax";
+  if (c->dim == 2 && (!(c->ymax > c->ymin) || !std::isfinite(c->ymax - c->ymin))) return "need ymin < ymax";
+  if (!(c->gamma > 1.0 && c->gamma <= 3.0)) return "gamma must be in (1, 3]";
+  if (!(c->cfl > 0.0 && c->cfl <= 1.0)) return "cfl must be in (0, 1]";
+  if (c->limiter == LF_LIMITER_SWEBY && !(c->beta >= 1.0 && c->beta <= 2.0)) return "beta must be in [1, 2]";
+  return nullptr;
+}
+
+// Event pair for the next traced launch (pool grows in chunks outside the
+// launch path as far as possible).
+lf_status trace_begin(lf_ctx* c, int stage, cudaEvent_t* stop) {
+  if (c->ev_used * 2 + 2 > c->ev_pool.size()) {
+    for (int k = 0; k < 256; ++k) {
+      cudaEvent_t e;
+      LF_CUDA(c, cudaEventCreate(&e));
+      c->ev_pool.push_back(e);
+    }
+  }
+  cudaEvent_t start = c->ev_pool[c->ev_used * 2];
+  *stop = c->ev_pool[c->ev_used * 2 + 1];
+  c->ev_stage.resize(c->ev_used + 1);
+  c->ev_stage[c->ev_used] = stage;
+  ++c->ev_used;
+  LF_CUDA(c, cudaEventRecord(start, c->stream));
+  return LF_OK;
+}
+
+template <typename T>
+lf_status dispatch_stage(lf_ctx* c, int stage) {
+  T* U = static_cast<T*>(c->U);
+  T* Us = static_cast<T*>(c->Ustar);
+  cudaEvent_t stop = nullptr;
+  if (c->profiling)
+    if (lf_status st = trace_begin(c, stage, &stop)) return st;
+  cudaError_t e = stage == 0 ? lf::launch_stage<T>(0, c->mesh, U, U, Us, c->sc, c->stream)
+                             : lf::launch_stage<T>(1, c->mesh, Us, U, U, c->sc, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, stage == 0 ? "predictor launch" : "corrector launch");
+  if (stop) LF_CUDA(c, cudaEventRecord(stop, c->stream));
+  return LF_OK;
+}
+
+// begin (dt) -> predictor -> corrector -> end (t, steps, parity)
+lf_status enqueue_step(lf_ctx* c, double dt_fixed) {
+  LF_CUDA(c, lf::launch_begin_step(c->sc, dt_fixed, c->stream));
+  for (int stage = 0; stage < 2; ++stage) {
+    lf_status st = c->elem == 8 ? dispatch_stage<double>(c, stage) : dispatch_stage<float>(c, stage);
+    if (st != LF_OK) return st;
+  }
+  LF_CUDA(c, lf::launch_end_step(c->sc, c->stream));
+  return LF_OK;
+}
+
+lf_status read_scalars(lf_ctx* c) {
+  LF_CUDA(c, cudaMemcpyAsync(c->hsc, c->sc, sizeof(lf::Scalars), cudaMemcpyDeviceToHost, c->stream));
+  LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LF_OK;
+}
+
+lf_status device_error_status(lf_ctx* c) {
+  if (c->hsc->err & lf::ERR_NONPHYSICAL) {
+    set_err(c, "non-positive density or pressure (or NaN) in the state");
+    return LF_ERR_NONPHYSICAL;
+  }
+  if (c->hsc->err & lf::ERR_BAD_DT) {
+    set_err(c, "non-finite or non-positive CFL time step");
+    return LF_ERR_NONPHYSICAL;
+  }
+  return LF_OK;
+}
+
+// Fresh time loop on the state just written into c->U.
+lf_status restart_clock(lf_ctx* c) {
+  LF_CUDA(c, lf::launch_reset_scalars(c->sc, c->cfg.cfl, c->stream));
+  cudaError_t e = c->elem == 8 ? lf::launch_wave_speed<double>(c->mesh, static_cast<double*>(c->U), c->sc, c->stream)
+                               : lf::launch_wave_speed<float>(c->mesh, static_cast<float*>(c->U), c->sc, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "wave speed launch");
+  c->has_state = true;
+  return LF_OK;
+}
+
+char* plane_ptr(lf_ctx* c, void* base, int l) {
+  return static_cast<char*>(base) + (size_t)l * c->mesh.plane * c->elem;
+}
+
+lf_status copy_plane_in(lf_ctx* c, int l, const void* src, cudaMemcpyKind kind) {
+  const size_t w = (size_t)c->mesh.nx * c->elem;
+  char* dst = plane_ptr(c, c->U, l);
+  if (!src) {
+    LF_CUDA(c, cudaMemset2DAsync(dst, (size_t)c->mesh.pitch * c->elem, 0, w, c->mesh.ny, c->stream));
+    return LF_OK;
+  }
+  LF_CUDA(c, cudaMemcpy2DAsync(dst, (size_t)c->mesh.pitch * c->elem, src, w, w, c->mesh.ny, kind, c->stream));
+  return LF_OK;
+}
+
+lf_status copy_plane_out(lf_ctx* c, int l, void* dst, cudaMemcpyKind kind) {
+  if (!dst) return LF_OK;
+  const size_t w = (size_t)c->mesh.nx * c->elem;
+  LF_CUDA(c, cudaMemcpy2DAsync(dst, w, plane_ptr(c, c->U, l), (size_t)c->mesh.pitch * c->elem, w, c->mesh.ny,
+                               kind, c->stream));
+  return LF_OK;
+}
+
+lf_status ensure_staging(lf_ctx* c) {
+  if (c->staging) return LF_OK;
+  LF_CUDA(c, cudaMalloc(&c->staging, 4 * (size_t)c->mesh.nx * c->mesh.ny * c->elem));
+  return LF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lf_status_string(lf_status s) {
+  switch (s) {
+    case LF_OK: return "LF_OK";
+    case LF_ERR_ARG: return "LF_ERR_ARG";
+    case LF_ERR_CUDA: return "LF_ERR_CUDA";
+    case LF_ERR_OOM: return "LF_ERR_OOM";
+    case LF_ERR_NONPHYSICAL: return "LF_ERR_NONPHYSICAL";
+    case LF_ERR_TIMEOUT: return "LF_ERR_TIMEOUT";
+    case LF_ERR_STATE: return "LF_ERR_STATE";
+  }
+  return "LF_ERR_UNKNOWN";
+}
+
+const char* lf_last_error(const lf_ctx* ctx) { return ctx ? ctx->last_error : g_init_error; }
+
+void lf_destroy(lf_ctx* c) {
+  if (!c) return;
+  {
+    DeviceGuard g(c->cfg.device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaFree(c->U);
+    cudaFree(c->Ustar);
+    cudaFree(c->staging);
+    cudaFree(c->sc);
+    cudaFree(c->partials);
+    cudaFree(c->dsums);
+    cudaFreeHost(c->hsc);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  }
+  delete c;
+}
+
+lf_status lf_init(const lf_config* cfg, void* stream, lf_ctx** out) {
+  if (!out) {
+    set_err(nullptr, "out is NULL");
+    return LF_ERR_ARG;
+  }
+  if (const char* why = validate(cfg)) {
+    set_err(nullptr, "invalid configuration: %s", why);
+    return LF_ERR_ARG;
+  }
+  // Test hook: simulate a failed device allocation without touching the GPU.
+  if (const char* f = std::getenv("LF_TEST_FAIL_ALLOC")) {
+    if (f[0] && f[0] != '0') {
+      set_err(nullptr, "device allocation failed (simulated by LF_TEST_FAIL_ALLOC)");
+      return LF_ERR_OOM;
+    }
+  }
+  lf_ctx* c = new lf_ctx();
+  c->cfg = *cfg;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->elem = cfg->precision == LF_FP64 ? 8 : 4;
+  lf::MeshDesc& m = c->mesh;
+  m.nx = cfg->nx;
+  m.ny = cfg->ny;
+  const int align = 128 / (int)c->elem;  // rows start on 128-byte boundaries
+  m.pitch = (cfg->nx + align - 1) / align * align;
+  m.plane = (long long)m.pitch * m.ny;
+  m.dim = cfg->dim;
+  m.bc = cfg->bc;
+  m.limiter = cfg->limiter;
+  m.riemann = cfg->riemann;
+  m.gamma = cfg->gamma;
+  m.beta = cfg->limiter == LF_LIMITER_MINMOD ? 1.0 : cfg->beta;
+  m.rdx = cfg->nx / (cfg->xmax - cfg->xmin);
+  m.rdy = cfg->dim == 2 ? cfg->ny / (cfg->ymax - cfg->ymin) : 0.0;
+
+  DeviceGuard g(cfg->device);
+  if (!g.ok) {
+    set_err(nullptr, "cannot select CUDA device %d", cfg->device);
+    delete c;
+    return LF_ERR_CUDA;
+  }
+  const size_t state_bytes = 4 * (size_t)m.plane * c->elem;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&c->U, state_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->Ustar, state_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->sc, sizeof(lf::Scalars));
+  if (e == cudaSuccess) e = cudaMalloc(&c->partials, (size_t)lf::sums_blocks() * 4 * 2 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->dsums, 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->hsc, sizeof(lf::Scalars));
+  if (e == cudaSuccess) e = lf::launch_reset_scalars(c->sc, cfg->cfl, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->U, 0, state_bytes, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->Ustar, 0, state_bytes, c->stream);
+  if (e != cudaSuccess) {
+    lf_status st = cuda_fail(nullptr, e, "lf_init");
+    cudaGetLastError();
+    lf_destroy(c);
+    return st;
+  }
+  *out = c;
+  return LF_OK;
+}
+
+lf_status lf_set_state(lf_ctx* c, const void* rho, const void* rhou, const void* rhov, const void* rhoE,
+                       int on_device) {
+  if (!c) return LF_ERR_ARG;
+  if (!rho || !rhou || !rhoE || (c->cfg.dim == 2 && !rhov)) {
+    set_err(c, "lf_set_state: NULL plane");
+    return LF_ERR_ARG;
+  }
+  DeviceGuard g(c->cfg.device);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const void* src[4] = {rho, rhou, rhov, rhoE};
+  for (int l = 0; l < 4; ++l)
+    if (lf_status st = copy_plane_in(c, l, src[l], kind)) return st;
+  if (lf_status st = restart_clock(c)) return st;
+  if (!on_device) LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LF_OK;
+}
+
+lf_status lf_set_primitive(lf_ctx* c, const void* rho, const void* u, const void* v, const void* p,
+                           int on_device) {
+  if (!c) return LF_ERR_ARG;
+  if (!rho || !u || !p || (c->cfg.dim == 2 && !v)) {
+    set_err(c, "lf_set_primitive: NULL plane");
+    return LF_ERR_ARG;
+  }
+  DeviceGuard g(c->cfg.device);
+  const size_t n = (size_t)c->mesh.nx * c->mesh.ny;
+  const void* src[4] = {rho, u, v, p};
+  if (!on_device) {
+    if (lf_status st = ensure_staging(c)) return st;
+    for (int l = 0; l < 4; ++l) {
+      char* dst = static_cast<char*>(c->staging) + l * n * c->elem;
+      if (src[l]) LF_CUDA(c, cudaMemcpyAsync(dst, src[l], n * c->elem, cudaMemcpyHostToDevice, c->stream));
+      else LF_CUDA(c, cudaMemsetAsync(dst, 0, n * c->elem, c->stream));
+      src[l] = dst;
+    }
+  }
+  cudaError_t e;
+  if (c->elem == 8)
+    e = lf::launch_prim_to_cons<double>(c->mesh, (const double*)src[0], (const double*)src[1],
+                                        (const double*)src[2], (const double*)src[3], (long long)n,
+                                        static_cast<double*>(c->U), c->stream);
+  else
+    e = lf::launch_prim_to_cons<float>(c->mesh, (const float*)src[0], (const float*)src[1], (const float*)src[2],
+                                       (const float*)src[3], (long long)n, static_cast<float*>(c->U), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "prim_to_cons launch");
+  if (lf_status st = restart_clock(c)) return st;
+  if (!on_device) LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LF_OK;
+}
+
+lf_status lf_get_state(lf_ctx* c, void* rho, void* rhou, void* rhov, void* rhoE, int on_device) {
+  if (!c) return LF_ERR_ARG;
+  if (!rho || !rhou || !rhoE || (c->cfg.dim == 2 && !rhov)) {
+    set_err(c, "lf_get_state: NULL plane");
+    return LF_ERR_ARG;
+  }
+  DeviceGuard g(c->cfg.device);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  void* dst[4] = {rho, rhou, rhov, rhoE};
+  for (int l = 0; l < 4; ++l)
+    if (lf_status st = copy_plane_out(c, l, dst[l], kind)) return st;
+  if (!on_device) LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LF_OK;
+}
+
+lf_status lf_get_primitive(lf_ctx* c, void* rho, void* u, void* v, void* p, int on_device) {
+  if (!c) return LF_ERR_ARG;
+  if (!rho || !u || !p || (c->cfg.dim == 2 && !v)) {
+    set_err(c, "lf_get_primitive: NULL plane");
+    return LF_ERR_ARG;
+  }
+  DeviceGuard g(c->cfg.device);
+  const size_t n = (size_t)c->mesh.nx * c->mesh.ny;
+  void* dst[4] = {rho, u, v, p};
+  void* kdst[4];
+  if (!on_device) {
+    if (lf_status st = ensure_staging(c)) return st;
+    for (int l = 0; l < 4; ++l) kdst[l] = static_cast<char*>(c->staging) + l * n * c->elem;
+  } else {
+    for (int l = 0; l < 4; ++l) kdst[l] = dst[l];
+  }
+  cudaError_t e;
+  if (c->elem == 8)
+    e = lf::launch_cons_to_prim<double>(c->mesh, static_cast<double*>(c->U), (double*)kdst[0], (double*)kdst[1],
+                                        (double*)kdst[2], (double*)kdst[3], c->stream);
+  else
+    e = lf::launch_cons_to_prim<float>(c->mesh, static_cast<float*>(c->U), (float*)kdst[0], (float*)kdst[1],
+                                       (float*)kdst[2], (float*)kdst[3], c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cons_to_prim launch");
+  if (!on_device) {
+    for (int l = 0; l < 4; ++l)
+      if (dst[l]) LF_CUDA(c, cudaMemcpyAsync(dst[l], kdst[l], n * c->elem, cudaMemcpyDeviceToHost, c->stream));
+    LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return LF_OK;
+}
+
+lf_status lf_step(lf_ctx* c, double* dt_out) {
+  if (!c) return LF_ERR_ARG;
+  if (!c->has_state) {
+    set_err(c, "lf_step: no state set");
+    return LF_ERR_STATE;
+  }
+  DeviceGuard g(c->cfg.device);
+  if (lf_status st = enqueue_step(c, 0.0)) return st;
+  if (dt_out) {
+    if (lf_status st = read_scalars(c)) return st;
+    *dt_out = c->hsc->dt;
+    return device_error_status(c);
+  }
+  return LF_OK;
+}
+
+lf_status lf_step_fixed(lf_ctx* c, double dt) {
+  if (!c) return LF_ERR_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt)) {
+    set_err(c, "lf_step_fixed: dt must be positive and finite");
+    return LF_ERR_ARG;
+  }
+  if (!c->has_state) {
+    set_err(c, "lf_step_fixed: no state set");
+    return LF_ERR_STATE;
+  }
+  DeviceGuard g(c->cfg.device);
+  return enqueue_step(c, dt);
+}
+
+lf_status lf_run(lf_ctx* c, double t_end, int32_t max_steps, int32_t* steps_done, double* t_out) {
+  if (!c) return LF_ERR_ARG;
+  if (max_steps < 0 || !std::isfinite(t_end)) {
+    set_err(c, "lf_run: max_steps must be >= 0 and t_end finite");
+    return LF_ERR_ARG;
+  }
+  if (!c->has_state) {
+    set_err(c, "lf_run: no state set");
+    return LF_ERR_STATE;
+  }
+  DeviceGuard g(c->cfg.device);
+  if (lf_status st = read_scalars(c)) return st;
+  const long long steps0 = c->hsc->steps;
+  LF_CUDA(c, lf::launch_set_t_end(c->sc, t_end > 0.0 ? t_end : 0.0, c->stream));
+  // Steps are enqueued in batches; with a final time the host polls t
+  // between batches, and steps past t_end are device-side no-ops.
+  const int batch = t_end > 0.0 ? 32 : max_steps;
+  int launched = 0;
+  lf_status st = LF_OK;
+  while (launched < max_steps) {
+    const int nb = max_steps - launched < batch ? max_steps - launched : batch;
+    for (int k = 0; k < nb && st == LF_OK; ++k) st = enqueue_step(c, 0.0);
+    if (st != LF_OK) break;
+    launched += nb;
+    if (t_end > 0.0 || launched >= max_steps) {
+      if ((st = read_scalars(c)) != LF_OK) break;
+      if (c->hsc->err || (t_end > 0.0 && c->hsc->t >= t_end)) break;
+    }
+  }
+  lf_status st2 = LF_OK;
+  if (cudaError_t e = lf::launch_set_t_end(c->sc, 0.0, c->stream)) st2 = cuda_fail(c, e, "set_t_end");
+  if (st == LF_OK) st = st2;
+  if (st == LF_OK) st = read_scalars(c);
+  if (st != LF_OK) return st;
+  if (steps_done) *steps_done = (int32_t)(c->hsc->steps - steps0);
+  if (t_out) *t_out = c->hsc->t;
+  return device_error_status(c);
+}
+
+lf_status lf_get_time(lf_ctx* c, double* t, int64_t* steps) {
+  if (!c) return LF_ERR_ARG;
+  DeviceGuard g(c->cfg.device);
+  if (lf_status st = read_scalars(c)) return st;
+  if (t) *t = c->hsc->t;
+  if (steps) *steps = c->hsc->steps;
+  return LF_OK;
+}
+
+lf_status lf_conservation_sums(lf_ctx* c, double out[4]) {
+  if (!c || !out) return LF_ERR_ARG;
+  DeviceGuard g(c->cfg.device);
+  cudaError_t e = c->elem == 8 ? lf::launch_sums<double>(c->mesh, static_cast<double*>(c->U), c->partials,
+                                                         lf::sums_blocks(), c->dsums, c->stream)
+                               : lf::launch_sums<float>(c->mesh, static_cast<float*>(c->U), c->partials,
+                                                        lf::sums_blocks(), c->dsums, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "sums launch");
+  LF_CUDA(c, cudaMemcpyAsync(out, c->dsums, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LF_OK;
+}
+
+lf_status lf_profile_enable(lf_ctx* c, int enable) {
+  if (!c) return LF_ERR_ARG;
+  DeviceGuard g(c->cfg.device);
+  LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->profiling = enable != 0;
+  c->ev_used = 0;
+  c->ev_stage.clear();
+  return LF_OK;
+}
+
+lf_status lf_profile_read(lf_ctx* c, double ms[2], int64_t launches[2]) {
+  if (!c || !ms || !launches) return LF_ERR_ARG;
+  DeviceGuard g(c->cfg.device);
+  LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  ms[0] = ms[1] = 0.0;
+  launches[0] = launches[1] = 0;
+  for (size_t k = 0; k < c->ev_used; ++k) {
+    float t = 0.0f;
+    LF_CUDA(c, cudaEventElapsedTime(&t, c->ev_pool[2 * k], c->ev_pool[2 * k + 1]));
+    ms[c->ev_stage[k]] += t;
+    launches[c->ev_stage[k]] += 1;
+  }
+  return LF_OK;
+}
+
+lf_status lf_sync(lf_ctx* c) {
+  if (!c) return LF_ERR_ARG;
+  DeviceGuard g(c->cfg.device);
+  if (lf_status st = read_scalars(c)) return st;
+  return device_error_status(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+// Device arithmetic of the Lagrange-flux scheme (arXiv:1607.08710):
+// equation of state (eq. 1), slope limiter (eq. "sweby"), Lagrangian HLL /
+// acoustic interface solver (eqs. 13-14) and upwind Lagrange flux (eq. 12).
+//
+// FP64 uses IEEE division and square root throughout.  FP32 uses the
+// hardware approximate reciprocal and reciprocal square root (__fdividef,
+// rsqrtf): each is within a few ulp, far inside the FP32 error budget of the
+// scheme, and keeps the special-function unit off the critical path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include "lf_internal.h"
+
+namespace lf {
+
+template <typename T> struct Ar;
+
+template <> struct Ar<double> {
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  // a = sqrt(x) and 1/a
+  static __device__ __forceinline__ void sqrt_and_rsqrt(double x, double& a, double& ia) {
+    a = sqrt(x);
+    ia = 1.0 / a;
+  }
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+};
+
+template <> struct Ar<float> {
+  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+  static __device__ __forceinline__ void sqrt_and_rsqrt(float x, float& a, float& ia) {
+    ia = rsqrtf(x);
+    a = x * ia;
+  }
+  static __device__ __forceinline__ float sqrt_(float x) { return x * rsqrtf(x); }
+};
+
+// Physics constants of one launch, in the kernel's precision.
+template <typename T>
+struct Phys {
+  T gamma, gm1, inv_gm1, beta, rdx, rdy;
+  int riemann;
+  __device__ __forceinline__ explicit Phys(const MeshDesc& m)
+      : gamma(T(m.gamma)), gm1(T(m.gamma - 1.0)), inv_gm1(T(1.0 / (m.gamma - 1.0))), beta(T(m.beta)),
+        rdx(T(m.rdx)), rdy(T(m.rdy)), riemann(m.riemann) {}
+};
+
+// Conservative (rho, rho u, rho v, rho E) -> primitive (rho, u, v, p), eq. (1).
+template <typename T>
+__device__ __forceinline__ void to_prim(const Phys<T>& P, const T U[4], T q[4]) {
+  T ir = Ar<T>::rcp(U[0]);
+  T u = U[1] * ir, v = U[2] * ir;
+  q[0] = U[0];
+  q[1] = u;
+  q[2] = v;
+  q[3] = P.gm1 * (U[3] - T(0.5) * (U[1] * u + U[2] * v));
+}
+
+// Eq. (sweby) for LIM_MINMOD / LIM_SWEBY, and van Leer's limiter.
+template <typename T, int LIM>
+__device__ __forceinline__ T limiter(T a, T b, T beta) {
+  T ab = a * b;
+  if (LIM == LIM_VANLEER) {
+    return ab > T(0) ? Ar<T>::div(T(2) * ab, a + b) : T(0);
+  } else {
+    T aa = fabs(a), bb = fabs(b);
+    T m;
+    if (LIM == LIM_MINMOD) m = fmin(aa, bb);
+    else m = fmax(fmin(aa, beta * bb), fmin(beta * aa, bb));
+    return ab > T(0) ? copysign(m, a) : T(0);
+  }
+}
+
+// Eqs. (13)-(14): star pressure and normal velocity at a face from the
+// reconstructed left/right (rho, u_n, p); then eq. (12) with the upwind state
+// chosen by the sign of u*.  DIR = 0: x-face (normal velocity u), 1: y-face.
+// qL, qR are primitive (rho, u, v, p).  F receives the flux along +x / +y.
+template <typename T, int DIR>
+__device__ __forceinline__ void lagrange_flux(const Phys<T>& P, const T qL[4], const T qR[4], T F[4]) {
+  const T rL = qL[0], pL = qL[3], rR = qR[0], pR = qR[3];
+  const T unL = qL[1 + DIR], unR = qR[1 + DIR];
+  T pstar, ustar;
+  if (P.riemann == RIEMANN_MAXC) {
+    // a = max(c_L, c_R) with c_k^2 = gamma p_k / rho_k; the larger c is the
+    // larger c^2, so only one square root is needed.
+    T a2 = P.gamma * fmax(Ar<T>::div(pL, rL), Ar<T>::div(pR, rR));
+    T a, ia;
+    Ar<T>::sqrt_and_rsqrt(a2, a, ia);
+    T irs = Ar<T>::rcp(rL + rR);
+    pstar = (rR * pL + rL * pR) * irs - rL * rR * irs * a * (unR - unL);
+    ustar = (rL * unL + rR * unR) * irs - (pR - pL) * irs * ia;
+  } else {
+    // acoustic solver with Z_k = rho_k c_k
+    T ZL = rL * Ar<T>::sqrt_(P.gamma * Ar<T>::div(pL, rL));
+    T ZR = rR * Ar<T>::sqrt_(P.gamma * Ar<T>::div(pR, rR));
+    T iZ = Ar<T>::rcp(ZL + ZR);
+    pstar = (ZR * pL + ZL * pR) * iZ - ZL * ZR * iZ * (unR - unL);
+    ustar = (ZL * unL + ZR * unR) * iZ - (pR - pL) * iZ;
+  }
+  const bool left = ustar > T(0);
+  const T r = left ? rL : rR;
+  const T u = left ? qL[1] : qR[1];
+  const T v = left ? qL[2] : qR[2];
+  const T p = left ? pL : pR;
+  const T rE = p * P.inv_gm1 + T(0.5) * r * (u * u + v * v);
+  const T m = r * ustar;
+  F[0] = m;
+  F[1] = m * u;
+  F[2] = m * v;
+  F[3] = (rE + pstar) * ustar;
+  F[1 + DIR] += pstar;
+}
+
+// Local CFL speed (|u|+c)/dx + (|v|+c)/dy (1D: (|u|+c)/dx) of a cell, and its
+// positivity (rho > 0 and p > 0; false for NaN).
+template <typename T, int DIM>
+__device__ __forceinline__ T cell_speed(const Phys<T>& P, const T U[4], bool& ok) {
+  T q[4];
+  to_prim(P, U, q);
+  ok = (q[0] > T(0)) && (q[3] > T(0));
+  T c = Ar<T>::sqrt_(P.gamma * Ar<T>::div(q[3], q[0]));
+  T s = (fabs(q[1]) + c) * P.rdx;
+  if (DIM == 2) s += (fabs(q[2]) + c) * P.rdy;
+  return s;
+}
+
+__device__ __forceinline__ int map_index(int c, int n, int bc) {
+  if (bc == BC_PERIODIC) {
+    c %= n;
+    return c < 0 ? c + n : c;
+  }
+  return c < 0 ? 0 : (c >= n ? n - 1 : c);
+}
+
+// Max of positive doubles through their IEEE bit patterns (which order like
+// the values); a NaN speed wins and is caught when dt is formed.
+__device__ __forceinline__ void atomic_max_speed(unsigned long long* dst, double s) {
+  atomicMax(dst, (unsigned long long)__double_as_longlong(s));
+}
+
+}  // namespace lf

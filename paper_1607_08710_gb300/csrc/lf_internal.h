@@ -1,0 +1,71 @@
+// Internal declarations shared by the CUDA translation units of liblagflux.
+// Not part of the public ABI (include/lagflux.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lf {
+
+// Device-resident scalars of one time loop.  dt never leaves the device
+// during a run; the host reads t and steps only between batches of steps.
+struct Scalars {
+  double t;                     // current time
+  double t_end;                 // final time (<= 0: none)
+  double dt;                    // dt of the step in progress (0: no-op step)
+  double cfl;                   // CFL number
+  unsigned long long smax[2];   // max wave speed, FP64 bits, double-buffered
+  long long steps;              // completed steps
+  int err;                      // sticky error bits (ERR_*)
+  int parity;                   // smax[parity] holds the max of the current state
+};
+
+enum : int { ERR_NONPHYSICAL = 1, ERR_BAD_DT = 2 };
+enum : int { LIM_MINMOD = 0, LIM_SWEBY = 1, LIM_VANLEER = 2 };
+enum : int { BC_TRANSMISSIVE = 0, BC_PERIODIC = 1 };
+enum : int { RIEMANN_MAXC = 0, RIEMANN_PER_SIDE = 1 };
+
+// Geometry and physics of one mesh, passed by value to every kernel.
+struct MeshDesc {
+  int nx, ny;        // cells
+  int pitch;         // elements between rows (>= nx)
+  long long plane;   // elements between field planes (>= pitch * ny)
+  int dim;           // 1 or 2
+  int bc;            // BC_*
+  int limiter;       // LIM_*
+  int riemann;       // RIEMANN_*
+  double gamma, beta;
+  double rdx, rdy;   // 1 / dx, 1 / dy
+};
+
+// Per-stage launch of the fused stage kernel (one Heun stage over the mesh).
+// stage 0: out = Uin - dt L(Uin)                      (predictor, Heun step 6)
+// stage 1: out = (Un + Uin)/2 - dt/2 L(Uin)           (corrector, Heun step 11),
+//          also accumulates the new state's max wave speed for the next dt.
+// `out` may alias `Un` (stage 1 updates in place); Uin must not alias out.
+template <typename T>
+cudaError_t launch_stage(int stage, const MeshDesc& m, const T* Uin, const T* Un, T* out,
+                         Scalars* sc, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_wave_speed(const MeshDesc& m, const T* U, Scalars* sc, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_prim_to_cons(const MeshDesc& m, const T* rho, const T* u, const T* v, const T* p,
+                                long long src_plane_stride, T* U, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_cons_to_prim(const MeshDesc& m, const T* U, T* rho, T* u, T* v, T* p, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_sums(const MeshDesc& m, const T* U, double* partials, int nblocks, double* out,
+                        cudaStream_t s);
+
+cudaError_t launch_begin_step(Scalars* sc, double dt_fixed, cudaStream_t s);
+cudaError_t launch_end_step(Scalars* sc, cudaStream_t s);
+cudaError_t launch_reset_scalars(Scalars* sc, double cfl, cudaStream_t s);
+cudaError_t launch_set_t_end(Scalars* sc, double t_end, cudaStream_t s);
+
+int sums_blocks();
+
+}  // namespace lf

@@ -1,0 +1,60 @@
+// Host launchers of the per-precision kernels.  Included by one translation
+// unit per precision, which instantiates them with LF_INSTANTIATE_LAUNCHERS.
+#pragma once
+
+#include "lf_aux.cuh"
+#include "lf_stage.cuh"
+
+namespace lf {
+
+inline int aux_blocks(long long n) {
+  long long b = (n + AUX_THREADS - 1) / AUX_THREADS;
+  if (b > 152 * 16) b = 152 * 16;
+  return b < 1 ? 1 : (int)b;
+}
+
+template <typename T>
+cudaError_t launch_stage(int stage, const MeshDesc& m, const T* Uin, const T* Un, T* out, Scalars* sc,
+                         cudaStream_t s) {
+  return launch_stage_impl<T>(stage, m, Uin, Un, out, sc, s);
+}
+
+template <typename T>
+cudaError_t launch_wave_speed(const MeshDesc& m, const T* U, Scalars* sc, cudaStream_t s) {
+  const int nb = aux_blocks((long long)m.nx * m.ny);
+  if (m.dim == 1) wave_speed_kernel<T, 1><<<nb, AUX_THREADS, 0, s>>>(m, U, sc);
+  else wave_speed_kernel<T, 2><<<nb, AUX_THREADS, 0, s>>>(m, U, sc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prim_to_cons(const MeshDesc& m, const T* rho, const T* u, const T* v, const T* p,
+                                long long, T* U, cudaStream_t s) {
+  prim_to_cons_kernel<T><<<aux_blocks((long long)m.nx * m.ny), AUX_THREADS, 0, s>>>(m, rho, u, v, p, U);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cons_to_prim(const MeshDesc& m, const T* U, T* rho, T* u, T* v, T* p, cudaStream_t s) {
+  cons_to_prim_kernel<T><<<aux_blocks((long long)m.nx * m.ny), AUX_THREADS, 0, s>>>(m, U, rho, u, v, p);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sums(const MeshDesc& m, const T* U, double* partials, int nblocks, double* out,
+                        cudaStream_t s) {
+  sums_partial_kernel<T><<<nblocks, AUX_THREADS, 0, s>>>(m, U, partials);
+  sums_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, out);
+  return cudaGetLastError();
+}
+
+#define LF_INSTANTIATE_LAUNCHERS(T)                                                                    \
+  template cudaError_t launch_stage<T>(int, const MeshDesc&, const T*, const T*, T*, Scalars*,         \
+                                       cudaStream_t);                                                  \
+  template cudaError_t launch_wave_speed<T>(const MeshDesc&, const T*, Scalars*, cudaStream_t);        \
+  template cudaError_t launch_prim_to_cons<T>(const MeshDesc&, const T*, const T*, const T*, const T*, \
+                                              long long, T*, cudaStream_t);                            \
+  template cudaError_t launch_cons_to_prim<T>(const MeshDesc&, const T*, T*, T*, T*, T*, cudaStream_t); \
+  template cudaError_t launch_sums<T>(const MeshDesc&, const T*, double*, int, double*, cudaStream_t);
+
+}  // namespace lf

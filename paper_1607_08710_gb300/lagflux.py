@@ -1,0 +1,267 @@
+"""Python binding of liblagflux (include/lagflux.h).
+
+Argument marshalling only: every step of the scheme runs in the CUDA library.
+The functions below carry the C names; `LagrangeFlux` wraps one context for
+torch users (device tensors are passed by data_ptr on torch's current stream).
+There is no CPU fallback: if the library is missing, importing raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblagflux.so")
+
+LF_OK, LF_ERR_ARG, LF_ERR_CUDA, LF_ERR_OOM, LF_ERR_NONPHYSICAL, LF_ERR_TIMEOUT, LF_ERR_STATE = range(7)
+LIMITERS = {"minmod": 0, "sweby": 1, "vanleer": 2}
+BCS = {"transmissive": 0, "periodic": 1}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+RIEMANN = {"maxc": 0, "per_side": 1}
+
+
+class lf_config(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int32),
+        ("nx", ctypes.c_int32),
+        ("ny", ctypes.c_int32),
+        ("limiter", ctypes.c_int32),
+        ("bc", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("riemann", ctypes.c_int32),
+        ("device", ctypes.c_int32),
+        ("xmin", ctypes.c_double),
+        ("xmax", ctypes.c_double),
+        ("ymin", ctypes.c_double),
+        ("ymax", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("beta", ctypes.c_double),
+    ]
+
+
+_vp, _i32, _i64, _d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_P = ctypes.POINTER
+
+# name -> (restype, argtypes); mirrors include/lagflux.h
+SIGNATURES = {
+    "lf_init": (ctypes.c_int, [_P(lf_config), _vp, _P(_vp)]),
+    "lf_destroy": (None, [_vp]),
+    "lf_set_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
+    "lf_set_primitive": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
+    "lf_get_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
+    "lf_get_primitive": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
+    "lf_step": (ctypes.c_int, [_vp, _P(_d)]),
+    "lf_step_fixed": (ctypes.c_int, [_vp, _d]),
+    "lf_run": (ctypes.c_int, [_vp, _d, _i32, _P(_i32), _P(_d)]),
+    "lf_get_time": (ctypes.c_int, [_vp, _P(_d), _P(_i64)]),
+    "lf_conservation_sums": (ctypes.c_int, [_vp, _P(_d)]),
+    "lf_sync": (ctypes.c_int, [_vp]),
+    "lf_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "lf_profile_read": (ctypes.c_int, [_vp, _P(_d), _P(_i64)]),
+    "lf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "lf_last_error": (ctypes.c_char_p, [_vp]),
+}
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"liblagflux.so not built at {path}; run paper_1607_08710_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = load_library()
+globals().update({name: getattr(_lib, name) for name in SIGNATURES})
+
+
+class LagrangeFluxError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_lib.lf_status_string(status).decode()}: {message}")
+        self.status = status
+
+
+@dataclass
+class Config:
+    nx: int
+    ny: int = 1
+    dim: int = 2
+    limiter: str = "vanleer"
+    bc: str = "transmissive"
+    precision: str = "fp64"
+    riemann: str = "maxc"
+    gamma: float = 1.4
+    cfl: float = 0.45
+    beta: float = 1.5
+    xmin: float = 0.0
+    xmax: float = 1.0
+    ymin: float = 0.0
+    ymax: float = 1.0
+    device: int = 0
+
+    def to_c(self) -> lf_config:
+        return lf_config(self.dim, self.nx, self.ny if self.dim == 2 else 1, LIMITERS[self.limiter], BCS[self.bc],
+                         PRECISIONS[self.precision], RIEMANN[self.riemann], self.device, self.xmin, self.xmax,
+                         self.ymin, self.ymax, self.gamma, self.cfl, self.beta)
+
+    @property
+    def np_dtype(self):
+        return np.float64 if self.precision == "fp64" else np.float32
+
+
+def _ptr_and_kind(a):
+    """(pointer, on_device) for a torch tensor or numpy array; None passes NULL."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+class LagrangeFlux:
+    """One mesh and its state on the GPU, advanced by the Lagrange-flux scheme."""
+
+    def __init__(self, cfg: Config, stream=None):
+        self.cfg = cfg
+        if stream is None:
+            try:
+                import torch
+
+                stream = torch.cuda.current_stream(cfg.device).cuda_stream if torch.cuda.is_available() else 0
+            except ImportError:
+                stream = 0
+        self._stream = stream
+        c = cfg.to_c()
+        h = ctypes.c_void_p()
+        st = _lib.lf_init(ctypes.byref(c), ctypes.c_void_p(stream), ctypes.byref(h))
+        if st != LF_OK:
+            raise LagrangeFluxError(st, _lib.lf_last_error(None).decode())
+        self._h = h
+
+    # -- helpers ---------------------------------------------------------
+    def _check(self, st: int):
+        if st != LF_OK:
+            raise LagrangeFluxError(st, _lib.lf_last_error(self._h).decode())
+
+    def _planes(self, planes, expect_device=None):
+        ptrs, kinds = [], set()
+        n = self.cfg.nx * (self.cfg.ny if self.cfg.dim == 2 else 1)
+        for a in planes:
+            p, k = _ptr_and_kind(a)
+            if a is not None:
+                if int(np.prod(a.shape)) != n:
+                    raise ValueError(f"plane has {int(np.prod(a.shape))} elements, expected {n}")
+                kinds.add(k)
+                self._check_dtype(a)
+            ptrs.append(p)
+        if len(kinds) != 1:
+            raise ValueError("all planes must be on the same side (all host or all device)")
+        return ptrs, kinds.pop()
+
+    def _check_dtype(self, a):
+        want = self.cfg.np_dtype
+        if isinstance(a, np.ndarray):
+            ok = a.dtype == want
+        else:
+            import torch
+
+            ok = a.dtype == (torch.float64 if want == np.float64 else torch.float32)
+        if not ok:
+            raise TypeError(f"buffer dtype {a.dtype} does not match precision {self.cfg.precision}")
+
+    # -- API -------------------------------------------------------------
+    def set_state(self, rho, rhou, rhov, rhoE):
+        p, k = self._planes([rho, rhou, rhov, rhoE])
+        self._check(_lib.lf_set_state(self._h, *p, k))
+
+    def set_primitive(self, rho, u, v, p):
+        ptrs, k = self._planes([rho, u, v, p])
+        self._check(_lib.lf_set_primitive(self._h, *ptrs, k))
+
+    def get_state(self, out=None):
+        """Conservative state as (4, ny, nx); `out` may be a torch CUDA tensor or numpy array."""
+        if out is None:
+            ny = self.cfg.ny if self.cfg.dim == 2 else 1
+            out = np.empty((4, ny, self.cfg.nx), dtype=self.cfg.np_dtype)
+        ptrs, k = self._planes([out[0], out[1], out[2], out[3]])
+        self._check(_lib.lf_get_state(self._h, *ptrs, k))
+        return out
+
+    def get_primitive(self, out=None):
+        if out is None:
+            ny = self.cfg.ny if self.cfg.dim == 2 else 1
+            out = np.empty((4, ny, self.cfg.nx), dtype=self.cfg.np_dtype)
+        ptrs, k = self._planes([out[0], out[1], out[2], out[3]])
+        self._check(_lib.lf_get_primitive(self._h, *ptrs, k))
+        return out
+
+    def step(self, return_dt: bool = False):
+        if return_dt:
+            dt = ctypes.c_double()
+            self._check(_lib.lf_step(self._h, ctypes.byref(dt)))
+            return dt.value
+        self._check(_lib.lf_step(self._h, None))
+        return None
+
+    def step_fixed(self, dt: float):
+        self._check(_lib.lf_step_fixed(self._h, float(dt)))
+
+    def run(self, t_end: float = 0.0, max_steps: int = 2**31 - 1):
+        n = ctypes.c_int32()
+        t = ctypes.c_double()
+        self._check(_lib.lf_run(self._h, float(t_end), int(max_steps), ctypes.byref(n), ctypes.byref(t)))
+        return n.value, t.value
+
+    def time(self):
+        t, s = ctypes.c_double(), ctypes.c_int64()
+        self._check(_lib.lf_get_time(self._h, ctypes.byref(t), ctypes.byref(s)))
+        return t.value, s.value
+
+    def conservation_sums(self) -> np.ndarray:
+        out = (ctypes.c_double * 4)()
+        self._check(_lib.lf_conservation_sums(self._h, out))
+        return np.array(out[:])
+
+    def profile(self, enable: bool = True):
+        """Start (or stop) per-stage event timing; enabling resets the totals."""
+        self._check(_lib.lf_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """((ms_predictor, ms_corrector), (launches_predictor, launches_corrector))."""
+        ms = (ctypes.c_double * 2)()
+        n = (ctypes.c_int64 * 2)()
+        self._check(_lib.lf_profile_read(self._h, ms, n))
+        return (ms[0], ms[1]), (n[0], n[1])
+
+    def sync(self):
+        self._check(_lib.lf_sync(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

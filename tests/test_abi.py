@@ -1,0 +1,118 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+symbol declared in include/*.h, and rejects bad arguments before touching
+the device."""
+import ctypes
+import os
+import re
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def lib():
+    from paper_1607_08710_gb300 import build
+
+    build.build()
+    from paper_1607_08710_gb300 import lagflux
+
+    return lagflux
+
+
+def declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            text = open(os.path.join(inc, f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(lf_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_api():
+    names = declared_functions()
+    for required in ("lf_init", "lf_step", "lf_run", "lf_destroy", "lf_set_state", "lf_get_state"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True, text=True, check=True)
+    exported = set(re.findall(r"\sT\s+(lf_\w+)", out.stdout))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    cdll = ctypes.CDLL(lib.LIB_PATH)
+    for n in declared_functions():
+        assert hasattr(cdll, n)
+
+
+def test_binding_covers_every_declared_symbol(lib):
+    assert sorted(lib.SIGNATURES) == [n for n in declared_functions() if n in lib.SIGNATURES]
+    missing = [n for n in declared_functions() if n not in lib.SIGNATURES]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    assert lib.lf_status_string(0) == b"LF_OK"
+    assert lib.lf_status_string(4) == b"LF_ERR_NONPHYSICAL"
+    assert lib.lf_status_string(99) == b"LF_ERR_UNKNOWN"
+
+
+@pytest.mark.parametrize(
+    "field,value",
+    [("dim", 3), ("nx", 0), ("ny", 0), ("limiter", 7), ("bc", 2), ("precision", 5), ("riemann", 2), ("gamma", 1.0),
+     ("gamma", 3.5), ("cfl", 0.0), ("cfl", 1.5), ("beta", 2.5), ("xmax", 0.0), ("device", -1)],
+)
+def test_init_rejects_bad_config_without_gpu(lib, field, value):
+    cfg = lib.Config(nx=16, ny=16, limiter="sweby").to_c()
+    setattr(cfg, field, value)
+    h = ctypes.c_void_p()
+    st = lib.lf_init(ctypes.byref(cfg), None, ctypes.byref(h))
+    assert st == lib.LF_ERR_ARG
+    assert h.value is None
+    assert b"invalid configuration" in lib.lf_last_error(None)
+
+
+def test_init_rejects_1d_with_ny(lib):
+    cfg = lib.Config(nx=16, ny=4, dim=1).to_c()
+    cfg.ny = 4
+    h = ctypes.c_void_p()
+    assert lib.lf_init(ctypes.byref(cfg), None, ctypes.byref(h)) == lib.LF_ERR_ARG
+
+
+def test_null_arguments(lib):
+    cfg = lib.Config(nx=8, ny=8).to_c()
+    assert lib.lf_init(ctypes.byref(cfg), None, None) == lib.LF_ERR_ARG
+    assert lib.lf_step(None, None) == lib.LF_ERR_ARG
+    assert lib.lf_run(None, 0.0, 1, None, None) == lib.LF_ERR_ARG
+    assert lib.lf_set_state(None, None, None, None, None, 0) == lib.LF_ERR_ARG
+    lib.lf_destroy(None)  # no-op
+
+
+def test_simulated_allocation_failure():
+    # A fresh process so the environment hook is seen; no GPU is touched.
+    code = (
+        "import ctypes, sys; sys.path.insert(0, %r)\n"
+        "from paper_1607_08710_gb300 import lagflux as L\n"
+        "c = L.Config(nx=64, ny=64).to_c(); h = ctypes.c_void_p()\n"
+        "st = L.lf_init(ctypes.byref(c), None, ctypes.byref(h))\n"
+        "print(st, L.lf_last_error(None).decode())\n" % ROOT
+    )
+    env = dict(os.environ, LF_TEST_FAIL_ALLOC="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
+    st, msg = r.stdout.split(" ", 1)
+    assert int(st) == 3  # LF_ERR_OOM
+    assert "simulated" in msg
+
+
+def test_product_package_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1607_08710_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", text, flags=re.M), f
+                assert "lagflux_oracle" not in text and "liblagflux_oracle" not in text, f

@@ -1,0 +1,270 @@
+"""GPU (CUDA, through the C ABI) against the FP64 CPU oracle.
+
+Bars:
+  * FP64: relative L1 <= 1e-12 per conservative field after up to 100 steps
+    (the two sides differ only in rounding order and FMA contraction).
+  * FP32: relative L1 <= 2e-5 per field against the FP64 oracle on the same
+    input after tens of steps (single-precision rounding, ~6e-8 per
+    operation, grown through the run; the bound for the smooth-flow precision
+    study is 1e-5, checked in test_gpu_precision.py).
+Sizes span several 28-column warp strips and 64-row tiles with ragged tails.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1607_08710_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1607_08710_gb300.lagflux import Config, LagrangeFlux, LagrangeFluxError  # noqa: E402
+
+FP64_TOL = 1e-12
+FP32_TOL = 2e-5
+
+
+def rel_l1(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    den = np.abs(b).sum()
+    if den == 0.0:
+        return np.abs(a - b).sum() / max(a.size, 1)
+    return np.abs(a - b).sum() / den
+
+
+def gpu_run(prim, precision="fp64", steps=None, t_end=0.0, dts=None, host=False, **kw):
+    ny, nx = prim.shape[1], prim.shape[2]
+    dim = kw.pop("dim", 2 if ny > 1 else 1)
+    cfg = Config(nx=nx, ny=ny, dim=dim, precision=precision, **kw)
+    tdt = torch.float64 if precision == "fp64" else torch.float32
+    s = LagrangeFlux(cfg)
+    if host:
+        q = np.ascontiguousarray(prim.astype(cfg.np_dtype))
+        s.set_primitive(q[0], q[1], q[2], q[3])
+    else:
+        q = torch.from_numpy(prim).to("cuda", tdt)
+        s.set_primitive(q[0], q[1], q[2], q[3])
+    if dts is not None:
+        for dt in dts:
+            s.step_fixed(dt)
+        n, t = len(dts), None
+    else:
+        n, t = s.run(t_end=t_end, max_steps=steps if steps is not None else 2**31 - 1)
+    if host:
+        U = s.get_state().astype(np.float64)
+    else:
+        out = torch.empty((4, ny, nx), dtype=tdt, device="cuda")
+        s.get_state(out)
+        U = out.double().cpu().numpy()
+    tt, nsteps = s.time()
+    s.close()
+    return U, nsteps, tt
+
+
+def oracle_cfg(prim, **kw):
+    ny, nx = prim.shape[1], prim.shape[2]
+    dim = kw.pop("dim", 2 if ny > 1 else 1)
+    return O.OracleConfig(nx=nx, ny=ny, dim=dim, **kw)
+
+
+def assert_close(U, ref, tol):
+    for l in range(4):
+        e = rel_l1(U[l], ref[l])
+        assert e <= tol, f"field {l}: relative L1 {e:.3e} > {tol:.1e}"
+
+
+def test_sod_1000_cells_fp64():
+    prim = inputs.named_shock_tube("sod", 1000).stack()
+    kw = dict(limiter="minmod", cfl=0.5)
+    ref = O.run(oracle_cfg(prim, **kw), O.prim_to_cons(oracle_cfg(prim, **kw), prim), 10**6, t_end=0.2)
+    U, n, t = gpu_run(prim, t_end=0.2, **kw)
+    assert n == ref.steps
+    assert t == 0.2
+    assert_close(U, ref.U, FP64_TOL)
+
+
+@pytest.mark.parametrize("nx,ny,bc", [(256, 256, "transmissive"), (100, 77, "transmissive"), (128, 96, "periodic"),
+                                      (57, 130, "periodic")])
+def test_quadrant_fp64_100_steps(nx, ny, bc):
+    prim = inputs.quadrant(nx, ny, seed=nx + ny).stack()
+    kw = dict(limiter="vanleer", cfl=0.45, bc=bc)
+    oc = oracle_cfg(prim, **kw)
+    ref = O.run(oc, O.prim_to_cons(oc, prim), 100)
+    U, n, t = gpu_run(prim, steps=100, **kw)
+    assert n == 100
+    assert t == pytest.approx(ref.t, rel=1e-13)
+    assert_close(U, ref.U, FP64_TOL)
+
+
+@pytest.mark.parametrize("limiter,beta", [("minmod", 1.0), ("sweby", 1.5), ("sweby", 2.0), ("vanleer", 1.0)])
+@pytest.mark.parametrize("riemann", ["maxc", "per_side"])
+@pytest.mark.parametrize("bc", ["transmissive", "periodic"])
+def test_variants_fp64(limiter, beta, riemann, bc):
+    prim = inputs.kelvin_helmholtz(61, 45, seed=1).stack() if bc == "periodic" else inputs.quadrant(61, 45, seed=2).stack()
+    kw = dict(limiter=limiter, beta=beta, riemann=riemann, bc=bc, cfl=0.4)
+    oc = oracle_cfg(prim, **kw)
+    ref = O.run(oc, O.prim_to_cons(oc, prim), 30)
+    U, n, _ = gpu_run(prim, steps=30, **kw)
+    assert_close(U, ref.U, FP64_TOL)
+
+
+@pytest.mark.parametrize("name", ["sod", "two_rarefaction", "sonic_rarefaction", "shock_shock"])
+def test_paper_tubes_fp64(name):
+    prim = inputs.named_shock_tube(name, 400).stack()
+    kw = dict(limiter="sweby", beta=1.5 if name != "shock_shock" else 1.0, cfl=0.25)
+    oc = oracle_cfg(prim, **kw)
+    ref = O.run(oc, O.prim_to_cons(oc, prim), 10**6, t_end=0.16)
+    U, n, t = gpu_run(prim, t_end=0.16, **kw)
+    assert n == ref.steps and t == 0.16
+    assert_close(U, ref.U, FP64_TOL)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 3), (2, 2), (3, 29), (29, 3), (1, 28), (65, 1), (5, 57)])
+@pytest.mark.parametrize("bc", ["transmissive", "periodic"])
+def test_tiny_and_ragged_2d(shape, bc):
+    ny, nx = shape
+    prim = inputs.quadrant(nx, ny, seed=3).stack()
+    kw = dict(limiter="vanleer", bc=bc, cfl=0.4)
+    oc = oracle_cfg(prim, dim=2, **kw)
+    ref = O.run(oc, O.prim_to_cons(oc, prim), 10)
+    U, n, _ = gpu_run(prim, steps=10, dim=2, **kw)
+    assert_close(U, ref.U, FP64_TOL)
+
+
+@pytest.mark.parametrize("nx", [1, 2, 27, 28, 29, 113, 4096])
+def test_1d_sizes(nx):
+    prim = inputs.named_shock_tube("sod", nx).stack()
+    kw = dict(limiter="minmod", cfl=0.5, dim=1)
+    oc = oracle_cfg(prim, **kw)
+    ref = O.run(oc, O.prim_to_cons(oc, prim), 20)
+    U, n, _ = gpu_run(prim, steps=20, **kw)
+    assert_close(U, ref.U, FP64_TOL)
+
+
+def test_host_buffers_and_fixed_dt_replay():
+    prim = inputs.quadrant(90, 70, seed=5).stack()
+    kw = dict(limiter="vanleer", cfl=0.45)
+    oc = oracle_cfg(prim, **kw)
+    ref = O.run(oc, O.prim_to_cons(oc, prim), 25)
+    U, n, _ = gpu_run(prim, dts=ref.dts, host=True, **kw)
+    assert n == 25
+    assert_close(U, ref.U, FP64_TOL)
+
+
+@pytest.mark.parametrize("kind", ["quadrant", "kh", "wave"])
+def test_fp32_against_fp64_oracle(kind):
+    n = 96
+    if kind == "quadrant":
+        prim, bc = inputs.quadrant(n, n, seed=9).stack(), "transmissive"
+    elif kind == "kh":
+        prim, bc = inputs.kelvin_helmholtz(n, n, seed=9).stack(), "periodic"
+    else:
+        prim, bc = inputs.smooth_wave(n).stack(), "periodic"
+    kw = dict(limiter="vanleer", bc=bc, cfl=0.45)
+    oc = oracle_cfg(prim, **kw)
+    ref = O.run(oc, O.prim_to_cons(oc, prim), 40)
+    U, nsteps, _ = gpu_run(prim, precision="fp32", dts=ref.dts, **kw)
+    assert_close(U, ref.U, FP32_TOL)
+
+
+def test_fp64_conservation_periodic():
+    n = 200
+    prim = inputs.kelvin_helmholtz(n, n, seed=4).stack()
+    cfg = Config(nx=n, ny=n, bc="periodic", limiter="vanleer", cfl=0.45)
+    s = LagrangeFlux(cfg)
+    q = torch.from_numpy(prim).cuda()
+    s.set_primitive(q[0], q[1], q[2], q[3])
+    s0 = s.conservation_sums()
+    s.run(max_steps=100)
+    s1 = s.conservation_sums()
+    U = s.get_state()
+    exact = np.array([math.fsum(U[l].ravel()) for l in range(4)])
+    np.testing.assert_allclose(s1, exact, rtol=1e-15, atol=1e-15)
+    scale = np.array([np.abs(U[l]).sum() for l in range(4)])
+    assert np.all(np.abs(s1 - s0) <= 1e-13 * scale)
+    s.close()
+
+
+def test_nonphysical_state_is_flagged_and_time_stops():
+    prim = inputs.quadrant(64, 64, seed=1).stack()
+    prim[3, 10, 10] = -1.0  # negative pressure
+    s = LagrangeFlux(Config(nx=64, ny=64))
+    q = torch.from_numpy(prim).cuda()
+    s.set_primitive(q[0], q[1], q[2], q[3])
+    with pytest.raises(LagrangeFluxError) as ei:
+        s.run(max_steps=5)
+    assert ei.value.status == 4
+    t, steps = s.time()
+    assert steps == 0 and t == 0.0
+    s.close()
+
+
+def test_nan_state_is_flagged():
+    prim = inputs.quadrant(40, 40, seed=1).stack()
+    prim[0, 3, 3] = np.nan
+    s = LagrangeFlux(Config(nx=40, ny=40, precision="fp32"))
+    q = torch.from_numpy(prim).cuda().float()
+    s.set_primitive(q[0], q[1], q[2], q[3])
+    with pytest.raises(LagrangeFluxError):
+        s.run(max_steps=3)
+    s.close()
+
+
+def test_step_before_state_is_an_error():
+    s = LagrangeFlux(Config(nx=8, ny=8))
+    with pytest.raises(LagrangeFluxError) as ei:
+        s.step()
+    assert ei.value.status == 6
+    s.close()
+
+
+def _patch_oracle_step(U_full, ci, cj, dt, precision, radius=6, **kw):
+    """One oracle step on a periodic patch around (ci, cj); returns the centre cell."""
+    ny, nx = U_full.shape[1:]
+    ii = (np.arange(ci - radius, ci + radius + 1)) % nx
+    jj = (np.arange(cj - radius, cj + radius + 1)) % ny
+    patch = np.ascontiguousarray(U_full[:, jj][:, :, ii].astype(np.float64))
+    oc = O.OracleConfig(nx=2 * radius + 1, ny=2 * radius + 1, lx=(2 * radius + 1) / nx, ly=(2 * radius + 1) / ny,
+                        bc="transmissive", **kw)
+    return O.run(oc, patch, 1, dts=[dt]).U[:, radius, radius]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_full_size_8192_sampled_cells(precision):
+    """8192^2 periodic Kelvin-Helmholtz, the benchmark's launch configuration:
+    one GPU step checked at sampled cells against the oracle on a patch (a cell
+    after one step depends only on cells within 4 of it), and the GPU dt
+    against the oracle's CFL dt of the whole mesh."""
+    n = 8192
+    prim = inputs.kelvin_helmholtz(n, n, seed=0).stack()
+    kw = dict(limiter="vanleer", bc="periodic", cfl=0.45)
+    tdt = torch.float64 if precision == "fp64" else torch.float32
+    s = LagrangeFlux(Config(nx=n, ny=n, precision=precision, **kw))
+    q = torch.from_numpy(prim).to("cuda", tdt)
+    s.set_primitive(q[0], q[1], q[2], q[3])
+    del q
+    U0 = torch.empty((4, n, n), dtype=tdt, device="cuda")
+    s.get_state(U0)
+    U0h = U0.cpu().numpy()
+    del U0
+    dt = s.step(return_dt=True)
+    oc = O.OracleConfig(nx=n, ny=n, **kw)
+    dt_ref = O.cfl_dt(oc, U0h.astype(np.float64))
+    assert dt == pytest.approx(dt_ref, rel=1e-14 if precision == "fp64" else 1e-6)
+    U1 = torch.empty((4, n, n), dtype=tdt, device="cuda")
+    s.get_state(U1)
+    rng = np.random.default_rng(0)
+    samples = [(0, 0), (n - 1, n - 1), (0, n - 1), (n // 2, n // 4), (4095, 2048)]
+    samples += [tuple(v) for v in rng.integers(0, n, size=(27, 2))]
+    tol = 1e-13 if precision == "fp64" else 2e-6
+    for ci, cj in samples:
+        ref = _patch_oracle_step(U0h, ci, cj, dt, precision, **{k: v for k, v in kw.items() if k != "bc"})
+        got = U1[:, cj, ci].double().cpu().numpy()
+        scale = np.abs(ref).max()
+        assert np.abs(got - ref).max() <= tol * scale, (ci, cj, got, ref)
+    s.close()
