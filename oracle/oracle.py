@@ -91,24 +91,59 @@ def build(force: bool = False) -> str:
         return _LIB
 
 
+def _declare(lib):
+    P = ctypes.POINTER
+    d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
+    pd = P(d)
+    lib.oracle_limiter.argtypes = [P(_Cfg), i64, pd, pd, pd]
+    lib.oracle_interface_solve.argtypes = [P(_Cfg), i64, pd, pd, pd, pd]
+    lib.oracle_face_flux.argtypes = [P(_Cfg), ctypes.c_int, i64, pd, pd, pd]
+    lib.oracle_prim_to_cons.argtypes = [P(_Cfg), pd, pd]
+    lib.oracle_cons_to_prim.argtypes = [P(_Cfg), pd, pd]
+    lib.oracle_dt.argtypes = [P(_Cfg), pd, pd]
+    lib.oracle_residual.argtypes = [P(_Cfg), pd, pd]
+    lib.oracle_run.argtypes = [P(_Cfg), pd, i32, d, d, pd, pd, P(i32), pd]
+    lib.oracle_run_tangent.argtypes = [P(_Cfg), pd, pd, i32, pd, pd, pd]
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        P = ctypes.POINTER
-        d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
-        pd = P(d)
-        lib.oracle_limiter.argtypes = [P(_Cfg), i64, pd, pd, pd]
-        lib.oracle_interface_solve.argtypes = [P(_Cfg), i64, pd, pd, pd, pd]
-        lib.oracle_face_flux.argtypes = [P(_Cfg), ctypes.c_int, i64, pd, pd, pd]
-        lib.oracle_prim_to_cons.argtypes = [P(_Cfg), pd, pd]
-        lib.oracle_cons_to_prim.argtypes = [P(_Cfg), pd, pd]
-        lib.oracle_dt.argtypes = [P(_Cfg), pd, pd]
-        lib.oracle_residual.argtypes = [P(_Cfg), pd, pd]
-        lib.oracle_run.argtypes = [P(_Cfg), pd, i32, d, d, pd, pd, P(i32), pd]
-        lib.oracle_run_tangent.argtypes = [P(_Cfg), pd, pd, i32, pd, pd, pd]
-        _lib = lib
+        _lib = _declare(ctypes.CDLL(build()))
     return _lib
+
+
+def compile_variant(source_text: str, out_path: str, opt: str = "-O1") -> str:
+    """Compiles an edited copy of the oracle source (used by the mutation tests)."""
+    src = out_path[:-3] + ".cpp"
+    with open(src, "w") as f:
+        f.write(source_text)
+    subprocess.run(["g++", opt, "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", "-o", out_path, src],
+                   check=True, capture_output=True)
+    return out_path
+
+
+class use_library:
+    """Context manager: route every call of this module to another oracle build."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = _load()
+        _lib = _declare(ctypes.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+
+
+def source_text() -> str:
+    with open(_SRC) as f:
+        return f.read()
 
 
 def _ptr(a: np.ndarray | None):
