@@ -146,11 +146,42 @@ lf_status lf_sync(lf_ctx* ctx);
 lf_status lf_profile_enable(lf_ctx* ctx, int enable);
 lf_status lf_profile_read(lf_ctx* ctx, double ms[2], int64_t launches[2]);
 
+/* One Heun step that allocates no device memory (the paper has no
+ * counterpart; this is a deployment convenience).  For callers that must not
+ * call cudaMalloc -- code living inside another framework's memory manager,
+ * code that may not allocate in a time-critical loop (cudaMalloc/cudaFree can
+ * synchronise the device), hosts that reserve all GPU memory up front -- and
+ * so cannot use lf_init.  The predictor state U* and the step's scalars live
+ * in one static device array compiled into the library
+ * (LF_NOALLOC_SCRATCH_BYTES, held on every GPU that loads the library until
+ * the process exits).
+ *   cfg    : mesh and scheme, as for lf_init; nx*ny must not exceed
+ *            LF_NOALLOC_MAX_CELLS, else LF_ERR_ARG and nothing is launched.
+ *   U_in   : device buffer of 4 dense planes (rho, rho u, rho v, rho E), each
+ *            nx*ny elements of the configured precision, x fastest; read only.
+ *   U_out  : device buffer of the same layout receiving U^{n+1}; may equal
+ *            U_in (in-place step) but must not partially overlap it.
+ *   dt     : > 0 uses this time step; <= 0 uses the CFL time step of U_in.
+ *   dt_used: nullable; if given, the call synchronises `stream`, stores the dt
+ *            used and returns LF_ERR_NONPHYSICAL if the new state has a
+ *            non-positive density or pressure.  If NULL the call only
+ *            enqueues and reports no device-side error.
+ *   stream : cudaStream_t (NULL: default stream) on device cfg->device.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  All calls share
+ * the array: calls whose GPU work overlaps (e.g. on two streams) race.
+ * Error text: lf_last_error(NULL). */
+#define LF_NOALLOC_MAX_CELLS (1LL << 18)
+#define LF_NOALLOC_SCRATCH_BYTES (256 + 4 * 8 * LF_NOALLOC_MAX_CELLS)
+lf_status lf_step_noalloc(const lf_config* cfg, const void* U_in, void* U_out, double dt, double* dt_used,
+                          void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* lf_status_string(lf_status s);
 
 /* Description of the last failure on this context (static per context;
- * valid until the next call on it).  NULL ctx: the last lf_init failure. */
+ * valid until the next call on it).  NULL ctx: the last lf_init or
+ * lf_step_noalloc failure. */
 const char* lf_last_error(const lf_ctx* ctx);
 
 #ifdef __cplusplus

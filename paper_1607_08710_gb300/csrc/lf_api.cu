@@ -194,6 +194,13 @@ lf_status ensure_staging(lf_ctx* c) {
 
 }  // namespace
 
+void lf::set_init_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_init_error, sizeof(g_init_error), fmt, ap);
+  va_end(ap);
+}
+
 extern "C" {
 
 const char* lf_status_string(lf_status s) {

@@ -68,4 +68,7 @@ cudaError_t launch_set_t_end(Scalars* sc, double t_end, cudaStream_t s);
 
 int sums_blocks();
 
+// Sets the message returned by lf_last_error(NULL) (printf-style).
+void set_init_error(const char* fmt, ...);
+
 }  // namespace lf

@@ -1,0 +1,158 @@
+// lf_step_noalloc: one Heun step that allocates no device memory.
+//
+// Who needs this.  Some callers cannot call cudaMalloc: code that runs inside
+// another framework's memory manager, which owns all of the GPU's memory and
+// must not be bypassed; code that must not allocate inside a time-critical
+// loop, because cudaMalloc/cudaFree can synchronise the whole device; and
+// hosts that reserve the GPU's memory up front so that a later allocation
+// would fail.  lf_init allocates a context (two states and scalars), so it is
+// closed to them.  This entry point instead keeps its scratch -- the Heun
+// predictor state U* and the step's scalars -- in one fixed array compiled
+// into this library.
+//
+// The array is a file-scope static __device__ variable: every GPU that loads
+// the library holds it (LF_NOALLOC_SCRATCH_BYTES) until the process exits.
+// Host code cannot use the array's name as a device address (on the host it
+// is only a stand-in symbol), so the first call on each device looks up the
+// real address with cudaGetSymbolAddress, with that device current, checks
+// the result and caches it; later calls reuse it.  Because that lookup may
+// load the module, make the first call on a device before any stream capture.
+//
+// Every call shares the one array and the array keeps the previous call's
+// contents: each call clears the scalars it needs (dt, wave-speed maximum,
+// error flags) before use.  Two calls whose work overlaps on the GPU (e.g. on
+// different streams) race on the array and give undefined results.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
+#include "../../include/lagflux.h"
+#include "lf_internal.h"
+
+namespace {
+
+constexpr long long kMaxCells = LF_NOALLOC_MAX_CELLS;
+constexpr size_t kScalarBytes = 256;
+constexpr size_t kScratchBytes = kScalarBytes + 4 * (size_t)kMaxCells * sizeof(double);
+static_assert(sizeof(lf::Scalars) <= kScalarBytes, "scalars do not fit their slot");
+static_assert(kScratchBytes == LF_NOALLOC_SCRATCH_BYTES, "header and library disagree on the scratch size");
+
+// The scratch: [0, 256) step scalars, [256, ...) the predictor state U* as
+// four dense planes of nx*ny elements (FP64 or FP32).
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::once_flag g_once[kMaxDevices];
+cudaError_t g_setup_status[kMaxDevices];
+void* g_scratch_addr[kMaxDevices];
+
+// Once per device, with that device current: the device address of g_scratch.
+cudaError_t scratch_address(int dev, void** out) {
+  std::call_once(g_once[dev], [dev] {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    g_setup_status[dev] = e;
+    g_scratch_addr[dev] = e == cudaSuccess ? p : nullptr;
+  });
+  *out = g_scratch_addr[dev];
+  return g_setup_status[dev];
+}
+
+const char* check_config(const lf_config* c) {
+  if (!c) return "config is NULL";
+  if (c->dim != 1 && c->dim != 2) return "dim must be 1 or 2";
+  if (c->nx < 1 || c->ny < 1 || (c->dim == 1 && c->ny != 1)) return "bad mesh size";
+  if ((long long)c->nx * c->ny > kMaxCells) return "mesh larger than LF_NOALLOC_MAX_CELLS";
+  if (c->limiter < 0 || c->limiter > 2 || c->bc < 0 || c->bc > 1 || c->riemann < 0 || c->riemann > 1)
+    return "unknown limiter, boundary condition or interface solver";
+  if (c->precision != LF_FP64 && c->precision != LF_FP32) return "unknown precision";
+  if (c->device < 0 || c->device >= kMaxDevices) return "device out of range";
+  if (!(c->xmax > c->xmin) || (c->dim == 2 && !(c->ymax > c->ymin))) return "empty domain";
+  if (!(c->gamma > 1.0 && c->gamma <= 3.0) || !(c->cfl > 0.0 && c->cfl <= 1.0)) return "gamma or cfl out of range";
+  if (c->limiter == LF_LIMITER_SWEBY && !(c->beta >= 1.0 && c->beta <= 2.0)) return "beta out of range";
+  return nullptr;
+}
+
+template <typename T>
+cudaError_t enqueue(const lf::MeshDesc& m, const T* Uin, T* Uout, T* Ustar, lf::Scalars* sc, double dt,
+                    double cfl, cudaStream_t s) {
+  cudaError_t e = lf::launch_reset_scalars(sc, cfl, s);
+  if (e == cudaSuccess && !(dt > 0.0)) e = lf::launch_wave_speed<T>(m, Uin, sc, s);
+  if (e == cudaSuccess) e = lf::launch_begin_step(sc, dt > 0.0 ? dt : 0.0, s);
+  if (e == cudaSuccess) e = lf::launch_stage<T>(0, m, Uin, Uin, Ustar, sc, s);
+  if (e == cudaSuccess) e = lf::launch_stage<T>(1, m, Ustar, Uin, Uout, sc, s);
+  if (e == cudaSuccess) e = lf::launch_end_step(sc, s);
+  return e;
+}
+
+}  // namespace
+
+extern "C" lf_status lf_step_noalloc(const lf_config* cfg, const void* U_in, void* U_out, double dt,
+                                     double* dt_used, void* stream) {
+  if (const char* why = check_config(cfg)) {
+    lf::set_init_error("lf_step_noalloc: %s (limit %lld cells)", why, kMaxCells);
+    return LF_ERR_ARG;
+  }
+  if (!U_in || !U_out || !std::isfinite(dt)) {
+    lf::set_init_error("lf_step_noalloc: NULL state buffer or non-finite dt");
+    return LF_ERR_ARG;
+  }
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  if (prev != cfg->device && cudaSetDevice(cfg->device) != cudaSuccess) {
+    lf::set_init_error("lf_step_noalloc: cannot select device %d", cfg->device);
+    return LF_ERR_CUDA;
+  }
+  lf_status st = LF_OK;
+  void* base = nullptr;
+  cudaError_t e = scratch_address(cfg->device, &base);
+  if (e != cudaSuccess) {
+    lf::set_init_error("lf_step_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    st = LF_ERR_CUDA;
+  } else {
+    lf::MeshDesc m;
+    m.nx = cfg->nx;
+    m.ny = cfg->ny;
+    m.pitch = cfg->nx;
+    m.plane = (long long)cfg->nx * cfg->ny;
+    m.dim = cfg->dim;
+    m.bc = cfg->bc;
+    m.limiter = cfg->limiter;
+    m.riemann = cfg->riemann;
+    m.gamma = cfg->gamma;
+    m.beta = cfg->limiter == LF_LIMITER_MINMOD ? 1.0 : cfg->beta;
+    m.rdx = cfg->nx / (cfg->xmax - cfg->xmin);
+    m.rdy = cfg->dim == 2 ? cfg->ny / (cfg->ymax - cfg->ymin) : 0.0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    lf::Scalars* sc = static_cast<lf::Scalars*>(base);
+    void* ustar = static_cast<unsigned char*>(base) + kScalarBytes;
+    if (cfg->precision == LF_FP64)
+      e = enqueue<double>(m, static_cast<const double*>(U_in), static_cast<double*>(U_out),
+                          static_cast<double*>(ustar), sc, dt, cfg->cfl, s);
+    else
+      e = enqueue<float>(m, static_cast<const float*>(U_in), static_cast<float*>(U_out),
+                         static_cast<float*>(ustar), sc, dt, cfg->cfl, s);
+    if (e != cudaSuccess) {
+      lf::set_init_error("lf_step_noalloc: launch failed: %s", cudaGetErrorString(e));
+      st = LF_ERR_CUDA;
+    } else if (dt_used) {
+      lf::Scalars h;
+      e = cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        lf::set_init_error("lf_step_noalloc: %s", cudaGetErrorString(e));
+        st = LF_ERR_CUDA;
+      } else {
+        *dt_used = h.dt;
+        if (h.err) {
+          lf::set_init_error("lf_step_noalloc: non-positive density or pressure, or bad dt");
+          st = LF_ERR_NONPHYSICAL;
+        }
+      }
+    }
+  }
+  if (prev >= 0 && prev != cfg->device) cudaSetDevice(prev);
+  return st;
+}

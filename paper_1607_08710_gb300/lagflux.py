@@ -62,6 +62,7 @@ SIGNATURES = {
     "lf_sync": (ctypes.c_int, [_vp]),
     "lf_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lf_profile_read": (ctypes.c_int, [_vp, _P(_d), _P(_i64)]),
+    "lf_step_noalloc": (ctypes.c_int, [_P(lf_config), _vp, _vp, _d, _P(_d), _vp]),
     "lf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lf_last_error": (ctypes.c_char_p, [_vp]),
 }
