@@ -269,6 +269,7 @@ lf_status lf_init(const lf_config* cfg, void* stream, lf_ctx** out) {
   m.beta = cfg->limiter == LF_LIMITER_MINMOD ? 1.0 : cfg->beta;
   m.rdx = cfg->nx / (cfg->xmax - cfg->xmin);
   m.rdy = cfg->dim == 2 ? cfg->ny / (cfg->ymax - cfg->ymin) : 0.0;
+  m.vec = 1;  // pitch is a multiple of 128 bytes and the planes come from cudaMalloc
 
   DeviceGuard g(cfg->device);
   if (!g.ok) {

@@ -42,7 +42,7 @@ struct Phys {
   T gamma, gm1, inv_gm1, beta, rdx, rdy;
   int riemann;
   __device__ __forceinline__ explicit Phys(const MeshDesc& m)
-      : gamma(T(m.gamma)), gm1(T(m.gamma - 1.0)), inv_gm1(T(1.0 / (m.gamma - 1.0))), beta(T(m.beta)),
+      : gamma(T(m.gamma)), gm1(T(m.gamma - 1.0)), inv_gm1(T(1) / gm1), beta(T(m.beta)),
         rdx(T(m.rdx)), rdy(T(m.rdy)), riemann(m.riemann) {}
 };
 

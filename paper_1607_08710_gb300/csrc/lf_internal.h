@@ -36,6 +36,8 @@ struct MeshDesc {
   int riemann;       // RIEMANN_*
   double gamma, beta;
   double rdx, rdy;   // 1 / dx, 1 / dy
+  int vec;           // 1: pitch and plane even and every state buffer 16-byte
+                     // aligned, so two adjacent cells may be moved as one vector
 };
 
 // Per-stage launch of the fused stage kernel (one Heun stage over the mesh).

@@ -125,6 +125,8 @@ extern "C" lf_status lf_step_noalloc(const lf_config* cfg, const void* U_in, voi
     m.beta = cfg->limiter == LF_LIMITER_MINMOD ? 1.0 : cfg->beta;
     m.rdx = cfg->nx / (cfg->xmax - cfg->xmin);
     m.rdy = cfg->dim == 2 ? cfg->ny / (cfg->ymax - cfg->ymin) : 0.0;
+    // dense planes: vector access only when every row and plane start stays aligned
+    m.vec = (cfg->nx % 2 == 0) && ((uintptr_t)U_in % 16 == 0) && ((uintptr_t)U_out % 16 == 0);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     lf::Scalars* sc = static_cast<lf::Scalars*>(base);
     void* ustar = static_cast<unsigned char*>(base) + kScalarBytes;

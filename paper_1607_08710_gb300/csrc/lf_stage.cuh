@@ -1,52 +1,181 @@
 // Fused Heun stage of the Lagrange-flux scheme (arXiv:1607.08710, Sec. 4):
 // per cell, primitive conversion (eq. 1), limited MUSCL slopes in x and y
 // (eq. "sweby"), face states, the acoustic interface solve (eqs. 13-14), the
-// upwind Lagrange flux (eq. 12) and the conservative update -- in one kernel
-// per stage, with no face quantity ever written to memory.
+// upwind Lagrange flux (eq. 12) and the conservative update -- one kernel per
+// stage, no face quantity ever written to memory.
 //
-// Work decomposition.  A warp owns a strip of 32 consecutive columns: lanes
-// 2..29 produce output cells, lanes 0,1 and 30,31 are the two-cell halo the
-// 5-point MUSCL stencil needs, so x-neighbours are exchanged with warp
-// shuffles and nothing is staged in shared memory.  The warp marches up a
-// tile of rows, carrying the y-stencil (three rows of primitives, two rows of
-// y-slopes and the flux through the face below) in registers, so every
-// primitive, slope and face flux is computed once per cell (up to the halo
-// lanes and the two rows of y-halo at the bottom of a tile).  The next row is
-// prefetched one iteration ahead to cover memory latency.
+// Work decomposition.  A warp owns a strip of 32*CPL consecutive columns,
+// CPL cells per lane.  The two columns at each end are the halo the 5-point
+// MUSCL stencil needs, so a strip produces 32*CPL - 4 output columns and all
+// x-neighbour exchange is done with warp shuffles (no shared memory, no
+// __syncthreads).  The warp marches up a tile of rows carrying the y-stencil
+// in registers: primitives of three rows, y-slopes and the flux through the
+// face below, each in three slots indexed by row mod 3.  The march is
+// unrolled by three so the slots are compile-time register names and nothing
+// is copied from row to row.  The next row is prefetched one iteration ahead;
+// the conservative values of the row being updated are re-read (an L1 hit)
+// rather than carried.  Every primitive, slope and face flux is computed once
+// per cell, up to the 4 halo columns of a strip and the 2 halo rows below and
+// above a tile.
+//
+// Memory safety.  Every load index is mapped into [0, nx) x [0, ny) by the
+// boundary condition (clamp or wrap); vector loads/stores are used only when
+// both cells of the pair are inside the row; stores are issued only for
+// output cells (column < nx, row < ny).
 #pragma once
 
 #include "lf_device.cuh"
 
 namespace lf {
 
-constexpr int STRIP_OUT = 28;   // output columns per warp
-constexpr int STAGE_WARPS = 4;  // warps per CTA, side by side in x
-constexpr int STAGE_TY = 64;    // rows per CTA tile in 2D
+// Launch shape; the defaults were chosen by timing on GB300 and can be
+// overridden at build time for tuning sweeps.
+#ifndef LF_STAGE_WARPS
+#define LF_STAGE_WARPS 4
+#endif
+#ifndef LF_TY_F32
+#define LF_TY_F32 64
+#endif
+#ifndef LF_TY_F64
+#define LF_TY_F64 64
+#endif
+#ifndef LF_MIN_BLOCKS
+#define LF_MIN_BLOCKS 1
+#endif
+constexpr int STAGE_WARPS = LF_STAGE_WARPS;  // warps per CTA, side by side in x
 
-// Fluxes through the right (i+1/2) and left (i-1/2) x-faces of this lane's
-// cell, from the primitive state q of the lane's column (valid on lanes 2..29).
-template <typename T, int LIM>
-__device__ __forceinline__ void x_fluxes(const Phys<T>& P, const T q[4], T Fp[4], T Fm[4]) {
-  constexpr unsigned FULL = 0xffffffffu;
-  T qplus[4], qright[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const T qm = __shfl_up_sync(FULL, q[k], 1);
-    const T qp = __shfl_down_sync(FULL, q[k], 1);
-    const T s = limiter<T, LIM>(q[k] - qm, qp - q[k], P.beta);
-    qplus[k] = q[k] + T(0.5) * s;            // left state of face i+1/2
-    const T qminus = q[k] - T(0.5) * s;      // right state of face i-1/2
-    qright[k] = __shfl_down_sync(FULL, qminus, 1);  // right state of face i+1/2
+template <int CPL> struct StripGeom {
+  static constexpr int COLS = 32 * CPL;     // columns covered by a warp
+  static constexpr int OUT = 32 * CPL - 4;  // output columns per warp
+};
+
+// Rows are uniform across a warp; wrap or clamp without an integer division.
+__device__ __forceinline__ int map_row(int r, int n, int bc) {
+  if (bc == BC_PERIODIC) {
+    while (r < 0) r += n;
+    while (r >= n) r -= n;
+    return r;
   }
-  lagrange_flux<T, 0>(P, qplus, qright, Fp);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) Fm[k] = __shfl_up_sync(FULL, Fp[k], 1);
+  return r < 0 ? 0 : (r >= n ? n - 1 : r);
 }
 
-template <typename T>
-__device__ __forceinline__ void load_cell(const T* __restrict__ U, long long plane, long long idx, T out[4]) {
+template <typename T, int CPL> struct VecLoad;
+template <typename T> struct VecLoad<T, 1> {
+  static __device__ __forceinline__ void load(const T* __restrict__ p, T v[1]) { v[0] = __ldg(p); }
+  static __device__ __forceinline__ void load_plain(const T* p, T v[1]) { v[0] = *p; }
+  static __device__ __forceinline__ void store(T* p, const T v[1]) { *p = v[0]; }
+};
+template <> struct VecLoad<float, 2> {
+  static __device__ __forceinline__ void load(const float* __restrict__ p, float v[2]) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+  }
+  static __device__ __forceinline__ void load_plain(const float* p, float v[2]) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+  }
+  static __device__ __forceinline__ void store(float* p, const float v[2]) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  }
+};
+template <> struct VecLoad<double, 2> {
+  static __device__ __forceinline__ void load(const double* __restrict__ p, double v[2]) {
+    const double2 t = __ldg(reinterpret_cast<const double2*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+  }
+  static __device__ __forceinline__ void load_plain(const double* p, double v[2]) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+  }
+  static __device__ __forceinline__ void store(double* p, const double v[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+};
+
+// Per-lane column bookkeeping of a strip.
+template <int CPL> struct LaneCols {
+  int c0;           // first column of this lane (may be < 0 or >= nx)
+  int ic[CPL];      // boundary-mapped columns
+  bool vec_ok;      // all CPL columns inside [0, nx): one vector access
+  bool out[CPL];    // cell is an output cell of this strip (and column < nx)
+  bool any_out;
+};
+
+template <int CPL>
+__device__ __forceinline__ LaneCols<CPL> lane_cols(int i0, int lane, int nx, int bc, int vec) {
+  LaneCols<CPL> L;
+  L.c0 = i0 - 2 + CPL * lane;
+  L.any_out = false;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) out[k] = __ldg(U + k * plane + idx);
+  for (int j = 0; j < CPL; ++j) {
+    const int c = L.c0 + j;
+    L.ic[j] = map_index(c, nx, bc);
+    const int k = CPL * lane + j;  // position in the strip
+    L.out[j] = k >= 2 && k < 32 * CPL - 2 && c < nx;
+    L.any_out |= L.out[j];
+  }
+  L.vec_ok = (CPL == 1 || vec) && L.c0 >= 0 && L.c0 + CPL - 1 < nx;
+  return L;
+}
+
+// Conservative values of this lane's CPL cells in row `off` (= mapped row * pitch).
+template <typename T, int CPL>
+__device__ __forceinline__ void load_row(const T* const __restrict__ P[4], const LaneCols<CPL>& L, int off,
+                                         T U[CPL][4]) {
+  if (L.vec_ok) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      T v[CPL];
+      VecLoad<T, CPL>::load(P[k] + off + L.c0, v);
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) U[j][k] = v[j];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) U[j][k] = __ldg(P[k] + off + L.ic[j]);
+  }
+}
+
+// Fluxes through the x-faces of this lane's cells, from the primitive states
+// q of the lane's CPL columns in the current row.  Fl[j] / Fr[j]: left and
+// right face of cell j (valid for output cells).
+template <typename T, int LIM, int CPL>
+__device__ __forceinline__ void x_fluxes(const Phys<T>& P, const T q[CPL][4], T Fl[CPL][4], T Fr[CPL][4]) {
+  constexpr unsigned FULL = 0xffffffffu;
+  T qL[CPL][4], qR[CPL][4];  // qL[j]: left state of face j+1/2; qR[j]: right state of face j-1/2
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const T left = __shfl_up_sync(FULL, q[CPL - 1][k], 1);  // column c0-1
+    const T right = __shfl_down_sync(FULL, q[0][k], 1);     // column c0+CPL
+    T dminus = q[0][k] - left;
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+      const T dplus = (j + 1 < CPL ? q[j + 1][k] : right) - q[j][k];
+      const T s = limiter<T, LIM>(dminus, dplus, P.beta);
+      qL[j][k] = q[j][k] + T(0.5) * s;
+      qR[j][k] = q[j][k] - T(0.5) * s;
+      dminus = dplus;
+    }
+  }
+  // internal faces j+1/2 for j < CPL-1, then the face shared with the next lane
+#pragma unroll
+  for (int j = 0; j + 1 < CPL; ++j) {
+    lagrange_flux<T, 0>(P, qL[j], qR[j + 1], Fr[j]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Fl[j + 1][k] = Fr[j][k];
+  }
+  T qRnext[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) qRnext[k] = __shfl_down_sync(FULL, qR[0][k], 1);
+  lagrange_flux<T, 0>(P, qL[CPL - 1], qRnext, Fr[CPL - 1]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Fl[0][k] = __shfl_up_sync(FULL, Fr[CPL - 1][k], 1);
 }
 
 // Warp-level max and any(), then one atomic per warp.
@@ -62,117 +191,271 @@ __device__ __forceinline__ void publish_speed(Scalars* sc, int wpar, T smax, boo
   }
 }
 
+// ---------------------------------------------------------------------------
+// Asynchronous row staging.  Every row a warp reads from global memory is
+// copied with cp.async into a per-warp ring in shared memory a few rows ahead
+// of its use, so no registers hold data in flight and memory latency is
+// hidden behind the arithmetic of the rows in between.  Each lane copies and
+// later reads back only its own CPL cells, so a lane's cp.async.wait_group is
+// the only synchronisation needed (no __syncwarp / __syncthreads).
+// ---------------------------------------------------------------------------
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Ring geometry.  Input rows: at row r the march reads row r+2 (new
+// primitives) and row r (the cell values for the update) and issues row
+// r+4, so rows r .. r+4 are live: 5 buffers.  U^n rows (corrector): row r is
+// read and row r+2 issued: 3 buffers.  A buffer holds one row of the strip,
+// laid out [field][lane][cell].
+constexpr int RING_IN = 5, RING_UN = 3, AHEAD_IN = 4, AHEAD_UN = 2;
+
+template <typename T, int CPL> struct Ring {
+  static constexpr int ROW = 4 * 32 * CPL;  // elements per buffer
+  static __host__ __device__ constexpr int buffers(int stage) { return RING_IN + (stage ? RING_UN : 0); }
+  static __host__ __device__ constexpr size_t warp_bytes(int stage) { return (size_t)buffers(stage) * ROW * sizeof(T); }
+};
+
+// Copies this lane's cells of (mapped) row offset `off` into buffer `buf`.
+template <typename T, int CPL>
+__device__ __forceinline__ void issue_row(T* buf, const T* const P[4], const LaneCols<CPL>& L, int off, int lane) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T* dst = buf + (k * 32 + lane) * CPL;
+    const T* src = P[k] + off;
+    if (L.vec_ok) {
+      cp_async<CPL * sizeof(T)>(dst, src + L.c0);
+    } else {
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) cp_async<sizeof(T)>(dst + j, src + L.ic[j]);
+    }
+  }
+}
+
+// Same for the output cells only (row offset `off` inside the mesh).
+template <typename T, int CPL>
+__device__ __forceinline__ void issue_out_cells(T* buf, const T* const P[4], const LaneCols<CPL>& L, int off,
+                                                int lane) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T* dst = buf + (k * 32 + lane) * CPL;
+    const T* src = P[k] + off + L.c0;
+    if (L.vec_ok) {
+      cp_async<CPL * sizeof(T)>(dst, src);  // with vec_ok, all or none of the lane's cells are outputs
+    } else {
+#pragma unroll
+      for (int j = 0; j < CPL; ++j)
+        if (L.out[j]) cp_async<sizeof(T)>(dst + j, src + j);
+    }
+  }
+}
+
+template <typename T, int CPL>
+__device__ __forceinline__ void read_row(const T* buf, int lane, T V[CPL][4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T v[CPL];
+    VecLoad<T, CPL>::load_plain(buf + (k * 32 + lane) * CPL, v);
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) V[j][k] = v[j];
+  }
+}
+
+// State of the y-march: three register slots indexed by row mod 3.
+template <typename T, int CPL> struct March {
+  T q[3][CPL][4];  // primitives of rows r, r+1, r+2
+  T s[3][CPL][4];  // y-slopes
+  T G[3][CPL][4];  // G[slot(r)] = flux through face r-1/2
+};
+
+template <typename T, int STAGE, int CPL> struct StageArgs {
+  const T* P[4];  // Uin planes (read with halo)
+  const T* N[4];  // U^n planes (corrector, read at the cell)
+  T* O[4];        // output planes
+  T* ring_in;     // this warp's input ring
+  T* ring_un;     // this warp's U^n ring (corrector)
+  int j0;         // first row of the tile
+};
+
+__device__ __forceinline__ int ring_slot(int row, int j0, int n) { return (row - j0 + 2 * n) % n; }
+
+// One row of the march.  S = slot of row r in the register window.
+template <typename T, int LIM, int STAGE, int CPL, int S>
+__device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, const StageArgs<T, STAGE, CPL>& A,
+                                          const LaneCols<CPL>& L, March<T, CPL>& M, int lane, int r, int jend,
+                                          T cx, T cy, T& smax, bool& bad) {
+  constexpr int S1 = (S + 1) % 3, S2 = (S + 2) % 3;
+  constexpr int ROW = Ring<T, CPL>::ROW;
+  // the group issued two rows ago (input row r+2, U^n row r) has landed
+  cp_wait<1>();
+  {
+    T Ut[CPL][4];
+    read_row<T, CPL>(A.ring_in + ring_slot(r + 2, A.j0, RING_IN) * ROW, lane, Ut);
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) to_prim(P, Ut[j], M.q[S2][j]);
+  }
+  if (r + 2 < jend) {
+    issue_row<T, CPL>(A.ring_in + ring_slot(r + AHEAD_IN, A.j0, RING_IN) * ROW, A.P, L,
+                      map_row(r + AHEAD_IN, m.ny, m.bc) * m.pitch, lane);
+    if (STAGE == 1 && L.any_out)
+      issue_out_cells<T, CPL>(A.ring_un + ring_slot(r + AHEAD_UN, A.j0, RING_UN) * ROW, A.N, L,
+                              (r + AHEAD_UN) * m.pitch, lane);
+  }
+  cp_commit();
+  // y-slopes of row r+1 and the flux through face r+1/2
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    T Lq[4], Rq[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      M.s[S1][j][k] = limiter<T, LIM>(M.q[S1][j][k] - M.q[S][j][k], M.q[S2][j][k] - M.q[S1][j][k], P.beta);
+      Lq[k] = M.q[S][j][k] + T(0.5) * M.s[S][j][k];
+      Rq[k] = M.q[S1][j][k] - T(0.5) * M.s[S1][j][k];
+    }
+    lagrange_flux<T, 1>(P, Lq, Rq, M.G[S1][j]);
+  }
+  // x-faces of row r
+  T Fl[CPL][4], Fr[CPL][4];
+  x_fluxes<T, LIM, CPL>(P, M.q[S], Fl, Fr);
+  if (!L.any_out) return;
+  // update the output cells of row r
+  T U[CPL][4], Un[CPL][4];
+  read_row<T, CPL>(A.ring_in + ring_slot(r, A.j0, RING_IN) * ROW, lane, U);
+  if (STAGE == 1) read_row<T, CPL>(A.ring_un + ring_slot(r, A.j0, RING_UN) * ROW, lane, Un);
+  T W[CPL][4];
+#pragma unroll
+  for (int j = 0; j < CPL; ++j)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const T base = STAGE == 0 ? U[j][k] : T(0.5) * (Un[j][k] + U[j][k]);
+      W[j][k] = base - cx * (Fr[j][k] - Fl[j][k]) - cy * (M.G[S1][j][k] - M.G[S][j][k]);
+    }
+  const int off = r * m.pitch;
+  if (L.vec_ok) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      T v[CPL];
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) v[j] = W[j][k];
+      VecLoad<T, CPL>::store(A.O[k] + off + L.c0, v);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < CPL; ++j)
+      if (L.out[j])
+#pragma unroll
+        for (int k = 0; k < 4; ++k) A.O[k][off + L.c0 + j] = W[j][k];
+  }
+  if (STAGE == 1) {
+#pragma unroll
+    for (int j = 0; j < CPL; ++j)
+      if (L.out[j]) {
+        bool ok;
+        smax = fmax(smax, cell_speed<T, 2>(P, W[j], ok));
+        bad |= !ok;
+      }
+  }
+}
+
 // STAGE 0: out = Uin - dt L(Uin).  STAGE 1: out = (Un + Uin)/2 - dt/2 L(Uin).
-template <typename T, int LIM, int STAGE>
-__global__ void __launch_bounds__(STAGE_WARPS * 32)
+// Dynamic shared memory: STAGE_WARPS * Ring<T,CPL>::warp_bytes(STAGE).
+template <typename T, int LIM, int STAGE, int CPL, int TY>
+__global__ void __launch_bounds__(STAGE_WARPS * 32, LF_MIN_BLOCKS)
 stage2d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out, Scalars* sc) {
+  extern __shared__ __align__(16) unsigned char lf_stage_smem[];
   const double dtd = sc->dt;
   if (!(dtd > 0.0)) return;
   const int wpar = sc->parity ^ 1;
   const Phys<T> P(m);
-  const int lane = threadIdx.x & 31;
-  const int i0 = (blockIdx.x * STAGE_WARPS + (threadIdx.x >> 5)) * STRIP_OUT;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = (blockIdx.x * STAGE_WARPS + warp) * StripGeom<CPL>::OUT;
   if (i0 >= m.nx) return;  // whole warp
-  const int c = i0 - 2 + lane;
-  const int ic = map_index(c, m.nx, m.bc);
-  const bool writer = lane >= 2 && lane < 2 + STRIP_OUT && c < m.nx;
-  const int j0 = blockIdx.y * STAGE_TY;
-  const int jend = min(j0 + STAGE_TY, m.ny);
+  const LaneCols<CPL> L = lane_cols<CPL>(i0, lane, m.nx, m.bc, m.vec);
+  const int j0 = blockIdx.y * TY;
+  const int jend = min(j0 + TY, m.ny);
   const double hs = STAGE == 0 ? 1.0 : 0.5;
   const T cx = T(hs * dtd * m.rdx), cy = T(hs * dtd * m.rdy);
-  const long long pl = m.plane;
+  constexpr int ROW = Ring<T, CPL>::ROW;
+  StageArgs<T, STAGE, CPL> A;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    A.P[k] = Uin + k * m.plane;
+    A.N[k] = Un + k * m.plane;
+    A.O[k] = out + k * m.plane;
+  }
+  A.ring_in = reinterpret_cast<T*>(lf_stage_smem + warp * Ring<T, CPL>::warp_bytes(STAGE));
+  A.ring_un = A.ring_in + RING_IN * ROW;
+  A.j0 = j0;
 
-  auto row_index = [&](int r) -> long long { return (long long)map_index(r, m.ny, m.bc) * m.pitch + ic; };
-
-  // Prologue: rows j0-2 .. j0+1, the y-slopes of rows j0-1 and j0, and the
-  // flux through face j0-1/2.
-  T Ua[4], Ub[4], Uc[4], qa[4], qb[4], qc[4], sa[4], sb[4], Gm[4], Gp[4];
+  // Prologue.  Group 0: input rows j0-2 .. j0+1.  Group 1: input row j0+2 and
+  // U^n row j0.  Rows j0-2 .. j0+1 give the register window: primitives in
+  // slots (row - j0 + 3) % 3, y-slopes of rows j0-1 (slot 2) and j0 (slot 0),
+  // and the flux through face j0-1/2 (slot 0).  Group 2 (input row j0+3, U^n
+  // row j0+1) reuses row j0-2's buffer, so it is issued after that row is read.
+  for (int row = j0 - 2; row <= j0 + 1; ++row)
+    issue_row<T, CPL>(A.ring_in + ring_slot(row, j0, RING_IN) * ROW, A.P, L, map_row(row, m.ny, m.bc) * m.pitch,
+                      lane);
+  cp_commit();
+  issue_row<T, CPL>(A.ring_in + ring_slot(j0 + 2, j0, RING_IN) * ROW, A.P, L, map_row(j0 + 2, m.ny, m.bc) * m.pitch,
+                    lane);
+  if (STAGE == 1 && L.any_out) issue_out_cells<T, CPL>(A.ring_un + ring_slot(j0, j0, RING_UN) * ROW, A.N, L,
+                                                      j0 * m.pitch, lane);
+  cp_commit();
+  cp_wait<1>();
+  March<T, CPL> M;
   {
-    T Um2[4], Um1[4], qm2[4], qm1[4], sm1[4];
-    load_cell(Uin, pl, row_index(j0 - 2), Um2);
-    load_cell(Uin, pl, row_index(j0 - 1), Um1);
-    load_cell(Uin, pl, row_index(j0), Ua);
-    load_cell(Uin, pl, row_index(j0 + 1), Ub);
-    to_prim(P, Um2, qm2);
-    to_prim(P, Um1, qm1);
-    to_prim(P, Ua, qa);
-    to_prim(P, Ub, qb);
-    T L[4], R[4];
+    T Ut[CPL][4];
+    const int slot_of[4] = {1, 2, 0, 1};  // rows j0-2, j0-1, j0, j0+1 -> register slots
+    T qm2[CPL][4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      sm1[k] = limiter<T, LIM>(qm1[k] - qm2[k], qa[k] - qm1[k], P.beta);
-      sa[k] = limiter<T, LIM>(qa[k] - qm1[k], qb[k] - qa[k], P.beta);
-      L[k] = qm1[k] + T(0.5) * sm1[k];
-      R[k] = qa[k] - T(0.5) * sa[k];
+    for (int t = 0; t < 4; ++t) {
+      read_row<T, CPL>(A.ring_in + ring_slot(j0 - 2 + t, j0, RING_IN) * ROW, lane, Ut);
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) to_prim(P, Ut[j], t == 0 ? qm2[j] : M.q[slot_of[t]][j]);
     }
-    lagrange_flux<T, 1>(P, L, R, Gm);
-  }
-  T Unext[4];
-  load_cell(Uin, pl, row_index(j0 + 2), Unext);
-  T Unold[4], Unold_next[4];
-  if (STAGE == 1 && writer) {
-    const long long idx = (long long)j0 * m.pitch + c;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) Unold_next[k] = Un[k * pl + idx];
+    for (int j = 0; j < CPL; ++j) {
+      T Lq[4], Rq[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        M.s[2][j][k] = limiter<T, LIM>(M.q[2][j][k] - qm2[j][k], M.q[0][j][k] - M.q[2][j][k], P.beta);
+        M.s[0][j][k] = limiter<T, LIM>(M.q[0][j][k] - M.q[2][j][k], M.q[1][j][k] - M.q[0][j][k], P.beta);
+        Lq[k] = M.q[2][j][k] + T(0.5) * M.s[2][j][k];
+        Rq[k] = M.q[0][j][k] - T(0.5) * M.s[0][j][k];
+      }
+      lagrange_flux<T, 1>(P, Lq, Rq, M.G[0][j]);
+    }
   }
+  if (j0 + 1 < jend) {
+    issue_row<T, CPL>(A.ring_in + ring_slot(j0 + 3, j0, RING_IN) * ROW, A.P, L,
+                      map_row(j0 + 3, m.ny, m.bc) * m.pitch, lane);
+    if (STAGE == 1 && L.any_out)
+      issue_out_cells<T, CPL>(A.ring_un + ring_slot(j0 + 1, j0, RING_UN) * ROW, A.N, L, (j0 + 1) * m.pitch, lane);
+  }
+  cp_commit();
 
   T smax = T(0);
   bool bad = false;
-  for (int r = j0; r < jend; ++r) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) Uc[k] = Unext[k];
-    if (r + 1 < jend) load_cell(Uin, pl, row_index(r + 3), Unext);
-    if (STAGE == 1 && writer) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) Unold[k] = Unold_next[k];
-      if (r + 1 < jend) {
-        const long long idx = (long long)(r + 1) * m.pitch + c;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) Unold_next[k] = Un[k * pl + idx];
-      }
-    }
-    to_prim(P, Uc, qc);
-    T L[4], R[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      sb[k] = limiter<T, LIM>(qb[k] - qa[k], qc[k] - qb[k], P.beta);  // y-slope of row r+1
-      L[k] = qa[k] + T(0.5) * sa[k];
-      R[k] = qb[k] - T(0.5) * sb[k];
-    }
-    lagrange_flux<T, 1>(P, L, R, Gp);  // face r+1/2
-    T Fp[4], Fm[4];
-    x_fluxes<T, LIM>(P, qa, Fp, Fm);
-
-    if (writer) {
-      T Unew[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const T base = STAGE == 0 ? Ua[k] : T(0.5) * (Unold[k] + Ua[k]);
-        Unew[k] = base - cx * (Fp[k] - Fm[k]) - cy * (Gp[k] - Gm[k]);
-      }
-      const long long idx = (long long)r * m.pitch + c;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) out[k * pl + idx] = Unew[k];
-      if (STAGE == 1) {
-        bool ok;
-        smax = fmax(smax, cell_speed<T, 2>(P, Unew, ok));
-        bad |= !ok;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      Ua[k] = Ub[k];
-      Ub[k] = Uc[k];
-      qa[k] = qb[k];
-      qb[k] = qc[k];
-      sa[k] = sb[k];
-      Gm[k] = Gp[k];
-    }
+  for (int r = j0;;) {
+    march_row<T, LIM, STAGE, CPL, 0>(P, m, A, L, M, lane, r, jend, cx, cy, smax, bad);
+    if (++r >= jend) break;
+    march_row<T, LIM, STAGE, CPL, 1>(P, m, A, L, M, lane, r, jend, cx, cy, smax, bad);
+    if (++r >= jend) break;
+    march_row<T, LIM, STAGE, CPL, 2>(P, m, A, L, M, lane, r, jend, cx, cy, smax, bad);
+    if (++r >= jend) break;
   }
+  cp_wait_all();
   if (STAGE == 1) publish_speed(sc, wpar, smax, bad);
 }
 
-template <typename T, int LIM, int STAGE>
+// 1D: one row, no y-terms.
+template <typename T, int LIM, int STAGE, int CPL>
 __global__ void __launch_bounds__(STAGE_WARPS * 32)
 stage1d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out, Scalars* sc) {
   const double dtd = sc->dt;
@@ -180,50 +463,59 @@ stage1d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
   const int wpar = sc->parity ^ 1;
   const Phys<T> P(m);
   const int lane = threadIdx.x & 31;
-  const int i0 = (blockIdx.x * STAGE_WARPS + (threadIdx.x >> 5)) * STRIP_OUT;
+  const int i0 = (blockIdx.x * STAGE_WARPS + (threadIdx.x >> 5)) * StripGeom<CPL>::OUT;
   if (i0 >= m.nx) return;
-  const int c = i0 - 2 + lane;
-  const int ic = map_index(c, m.nx, m.bc);
-  const bool writer = lane >= 2 && lane < 2 + STRIP_OUT && c < m.nx;
+  const LaneCols<CPL> L = lane_cols<CPL>(i0, lane, m.nx, m.bc, m.vec);
   const T cx = T((STAGE == 0 ? 1.0 : 0.5) * dtd * m.rdx);
-  const long long pl = m.plane;
-  T U[4], q[4], Fp[4], Fm[4];
-  load_cell(Uin, pl, ic, U);
-  to_prim(P, U, q);
-  x_fluxes<T, LIM>(P, q, Fp, Fm);
+  const T* Pp[4] = {Uin, Uin + m.plane, Uin + 2 * m.plane, Uin + 3 * m.plane};
+  T U[CPL][4], q[CPL][4], Fl[CPL][4], Fr[CPL][4];
+  load_row<T, CPL>(Pp, L, 0, U);
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) to_prim(P, U[j], q[j]);
+  x_fluxes<T, LIM, CPL>(P, q, Fl, Fr);
   T smax = T(0);
   bool bad = false;
-  if (writer) {
-    T Unew[4];
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    if (!L.out[j]) continue;
+    const int c = L.c0 + j;
+    T W[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const T base = STAGE == 0 ? U[k] : T(0.5) * (Un[k * pl + c] + U[k]);
-      Unew[k] = base - cx * (Fp[k] - Fm[k]);
+      const T base = STAGE == 0 ? U[j][k] : T(0.5) * (Un[k * m.plane + c] + U[j][k]);
+      W[k] = base - cx * (Fr[j][k] - Fl[j][k]);
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) out[k * pl + c] = Unew[k];
+    for (int k = 0; k < 4; ++k) out[k * m.plane + c] = W[k];
     if (STAGE == 1) {
       bool ok;
-      smax = cell_speed<T, 1>(P, Unew, ok);
-      bad = !ok;
+      smax = fmax(smax, cell_speed<T, 1>(P, W, ok));
+      bad |= !ok;
     }
   }
   if (STAGE == 1) publish_speed(sc, wpar, smax, bad);
 }
 
+// Cells per lane and tile height per precision (FP64 keeps one cell per lane
+// to stay clear of register spills).
+template <typename T> struct StageShape { static constexpr int CPL = 2, TY = LF_TY_F32; };
+template <> struct StageShape<double> { static constexpr int CPL = 1, TY = LF_TY_F64; };
+
 template <typename T, int LIM>
 cudaError_t launch_stage_lim(int stage, const MeshDesc& m, const T* Uin, const T* Un, T* out, Scalars* sc,
                              cudaStream_t s) {
-  const int strips = (m.nx + STRIP_OUT - 1) / STRIP_OUT;
+  constexpr int CPL = StageShape<T>::CPL, TY = StageShape<T>::TY;
+  const int strips = (m.nx + StripGeom<CPL>::OUT - 1) / StripGeom<CPL>::OUT;
   dim3 block(STAGE_WARPS * 32);
   if (m.dim == 1) {
     dim3 grid((strips + STAGE_WARPS - 1) / STAGE_WARPS);
-    if (stage == 0) stage1d_kernel<T, LIM, 0><<<grid, block, 0, s>>>(m, Uin, Un, out, sc);
-    else stage1d_kernel<T, LIM, 1><<<grid, block, 0, s>>>(m, Uin, Un, out, sc);
+    if (stage == 0) stage1d_kernel<T, LIM, 0, CPL><<<grid, block, 0, s>>>(m, Uin, Un, out, sc);
+    else stage1d_kernel<T, LIM, 1, CPL><<<grid, block, 0, s>>>(m, Uin, Un, out, sc);
   } else {
-    dim3 grid((strips + STAGE_WARPS - 1) / STAGE_WARPS, (m.ny + STAGE_TY - 1) / STAGE_TY);
-    if (stage == 0) stage2d_kernel<T, LIM, 0><<<grid, block, 0, s>>>(m, Uin, Un, out, sc);
-    else stage2d_kernel<T, LIM, 1><<<grid, block, 0, s>>>(m, Uin, Un, out, sc);
+    dim3 grid((strips + STAGE_WARPS - 1) / STAGE_WARPS, (m.ny + TY - 1) / TY);
+    const size_t smem = STAGE_WARPS * Ring<T, CPL>::warp_bytes(stage);
+    if (stage == 0) stage2d_kernel<T, LIM, 0, CPL, TY><<<grid, block, smem, s>>>(m, Uin, Un, out, sc);
+    else stage2d_kernel<T, LIM, 1, CPL, TY><<<grid, block, smem, s>>>(m, Uin, Un, out, sc);
   }
   return cudaGetLastError();
 }

@@ -14,7 +14,8 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "liblagflux.so")
+# LAGFLUX_LIB selects another build of the same library (e.g. a tuning variant).
+LIB_PATH = os.environ.get("LAGFLUX_LIB") or os.path.join(_HERE, "liblagflux.so")
 
 LF_OK, LF_ERR_ARG, LF_ERR_CUDA, LF_ERR_OOM, LF_ERR_NONPHYSICAL, LF_ERR_TIMEOUT, LF_ERR_STATE = range(7)
 LIMITERS = {"minmod": 0, "sweby": 1, "vanleer": 2}

@@ -34,8 +34,9 @@ def rel_l1(a, b):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("fixed_dt", [False, True])
-def test_noalloc_matches_context_path_twice(precision, fixed_dt):
-    nx, ny = 200, 150
+@pytest.mark.parametrize("nx,ny", [(200, 150), (201, 151)])
+def test_noalloc_matches_context_path_twice(precision, fixed_dt, nx, ny):
+    # odd nx: dense rows start on odd cells, so the kernels must use per-cell access
     prim = inputs.quadrant(nx, ny, seed=21).stack()
     cfg = L.Config(nx=nx, ny=ny, precision=precision, limiter="vanleer", bc="transmissive", cfl=0.45)
     tdt = torch.float64 if precision == "fp64" else torch.float32
