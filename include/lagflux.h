@@ -146,6 +146,56 @@ lf_status lf_sync(lf_ctx* ctx);
 lf_status lf_profile_enable(lf_ctx* ctx, int enable);
 lf_status lf_profile_read(lf_ctx* ctx, double ms[2], int64_t launches[2]);
 
+/* ------------------------------------------------------------------------
+ * Batched mode: many independent 2D meshes of uneven sizes advanced together
+ * by the same Heun/RK2 Lagrange-flux step (Sec. 4), each problem with its own
+ * CFL time step, time and step count.  One persistent kernel launch per
+ * stage covers all problems; the step loop is recorded once as a CUDA graph.
+ * ------------------------------------------------------------------------ */
+typedef struct lf_batch lf_batch;
+
+/* cfgs[0..nprob-1]: one configuration per problem.  dim must be 2; nx, ny
+ * and the domain may differ; limiter, bc, precision, riemann, gamma, cfl,
+ * beta and device must be equal across problems.  Allocates two state pools
+ * (sum over problems of 4 planes, rows padded to 128 bytes), per-problem
+ * scalars and the work-unit table. */
+lf_status lf_batch_init(const lf_config* cfgs, int32_t nprob, void* stream, lf_batch** out);
+void lf_batch_destroy(lf_batch* b);
+
+/* Sets problem p's state from primitive planes (rho, u, v, p), each
+ * cfgs[p].nx * cfgs[p].ny elements, x fastest; resets that problem's time and
+ * step count and computes its first wave-speed maximum. */
+lf_status lf_batch_set_primitive(lf_batch* b, int32_t p, const void* rho, const void* u, const void* v,
+                                 const void* pr, int on_device);
+
+/* Copies out problem p's conservative planes. */
+lf_status lf_batch_get_state(lf_batch* b, int32_t p, void* rho, void* rhou, void* rhov, void* rhoE,
+                             int on_device);
+
+/* Enqueues nsteps Heun steps of every problem.  use_graph = 1: the loop of
+ * nsteps steps is recorded once as a CUDA graph (re-recorded when nsteps or
+ * the tile height changes) and replayed on the context's stream; 0: direct
+ * launches.  Does not synchronise.  Every problem must have a state. */
+lf_status lf_batch_run(lf_batch* b, int32_t nsteps, int32_t use_graph);
+
+/* Times trial_steps steps for each candidate tile height (rows per work
+ * unit: 16, 24, 32, 48, 64, 96, 128) on the current states, keeps the
+ * fastest and restores the states and times to what they were (the trial
+ * steps leave no trace).  Allocates a temporary copy of the state pool.
+ * chosen_rows (nullable) receives the pick.  Synchronises. */
+lf_status lf_batch_autotune(lf_batch* b, int32_t trial_steps, int32_t* chosen_rows);
+
+/* Sets the tile height directly (1 <= rows <= 4096). */
+lf_status lf_batch_set_rows(lf_batch* b, int32_t rows);
+
+/* Per-problem time and step count (arrays of nprob, nullable); synchronises
+ * and returns LF_ERR_NONPHYSICAL if any problem has raised a device error. */
+lf_status lf_batch_get_times(lf_batch* b, double* t, int64_t* steps);
+
+/* Description of the last failure on this batch (NULL: the last failed
+ * lf_batch_init). */
+const char* lf_batch_last_error(const lf_batch* b);
+
 /* One Heun step that allocates no device memory (the paper has no
  * counterpart; this is a deployment convenience).  For callers that must not
  * call cudaMalloc -- code living inside another framework's memory manager,

@@ -23,7 +23,10 @@ CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--exp
 
 # Per-file extra flags: the FP32 kernels flush denormals (FP32 values below
 # 1e-38 play no role in the scheme, and it keeps the special-function paths short).
-EXTRA = {"lf_kernels_f32.cu": ["-ftz=true"]}
+# Both kernel units pin their rounding (-fmad=false; fused multiply-adds are
+# written out where wanted), so results do not depend on how an expression
+# was inlined.
+EXTRA = {"lf_kernels_f32.cu": ["-ftz=true", "-fmad=false"], "lf_kernels_f64.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:

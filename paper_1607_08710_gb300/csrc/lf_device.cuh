@@ -36,6 +36,14 @@ template <> struct Ar<float> {
   static __device__ __forceinline__ float sqrt_(float x) { return x * rsqrtf(x); }
 };
 
+// Rounding is pinned: the kernels are compiled with -fmad=false, so a
+// product and a sum are fused only where fma_ is written.  Every inlined copy
+// of an expression (e.g. the first face of a row tile in its prologue and the
+// same face inside the previous tile's march) then rounds identically, which
+// makes results independent of the tile height and of the launch shape.
+__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+
 // Physics constants of one launch, in the kernel's precision.
 template <typename T>
 struct Phys {
@@ -54,7 +62,7 @@ __device__ __forceinline__ void to_prim(const Phys<T>& P, const T U[4], T q[4]) 
   q[0] = U[0];
   q[1] = u;
   q[2] = v;
-  q[3] = P.gm1 * (U[3] - T(0.5) * (U[1] * u + U[2] * v));
+  q[3] = P.gm1 * fma_(T(-0.5), fma_(U[1], u, U[2] * v), U[3]);
 }
 
 // Eq. (sweby) for LIM_MINMOD / LIM_SWEBY, and van Leer's limiter.
@@ -88,22 +96,22 @@ __device__ __forceinline__ void lagrange_flux(const Phys<T>& P, const T qL[4], c
     T a, ia;
     Ar<T>::sqrt_and_rsqrt(a2, a, ia);
     T irs = Ar<T>::rcp(rL + rR);
-    pstar = (rR * pL + rL * pR) * irs - rL * rR * irs * a * (unR - unL);
-    ustar = (rL * unL + rR * unR) * irs - (pR - pL) * irs * ia;
+    pstar = fma_(-(rL * rR * irs * a), unR - unL, fma_(rR, pL, rL * pR) * irs);
+    ustar = fma_(-((pR - pL) * irs), ia, fma_(rL, unL, rR * unR) * irs);
   } else {
     // acoustic solver with Z_k = rho_k c_k
     T ZL = rL * Ar<T>::sqrt_(P.gamma * Ar<T>::div(pL, rL));
     T ZR = rR * Ar<T>::sqrt_(P.gamma * Ar<T>::div(pR, rR));
     T iZ = Ar<T>::rcp(ZL + ZR);
-    pstar = (ZR * pL + ZL * pR) * iZ - ZL * ZR * iZ * (unR - unL);
-    ustar = (ZL * unL + ZR * unR) * iZ - (pR - pL) * iZ;
+    pstar = fma_(-(ZL * ZR * iZ), unR - unL, fma_(ZR, pL, ZL * pR) * iZ);
+    ustar = fma_(-(pR - pL), iZ, fma_(ZL, unL, ZR * unR) * iZ);
   }
   const bool left = ustar > T(0);
   const T r = left ? rL : rR;
   const T u = left ? qL[1] : qR[1];
   const T v = left ? qL[2] : qR[2];
   const T p = left ? pL : pR;
-  const T rE = p * P.inv_gm1 + T(0.5) * r * (u * u + v * v);
+  const T rE = fma_(p, P.inv_gm1, T(0.5) * r * fma_(u, u, v * v));
   const T m = r * ustar;
   F[0] = m;
   F[1] = m * u;
@@ -121,7 +129,7 @@ __device__ __forceinline__ T cell_speed(const Phys<T>& P, const T U[4], bool& ok
   ok = (q[0] > T(0)) && (q[3] > T(0));
   T c = Ar<T>::sqrt_(P.gamma * Ar<T>::div(q[3], q[0]));
   T s = (fabs(q[1]) + c) * P.rdx;
-  if (DIM == 2) s += (fabs(q[2]) + c) * P.rdy;
+  if (DIM == 2) s = fma_(fabs(q[2]) + c, P.rdy, s);
   return s;
 }
 

@@ -40,6 +40,26 @@ struct MeshDesc {
                      // aligned, so two adjacent cells may be moved as one vector
 };
 
+// Batched mode: many independent 2D meshes share one pool per state.  Each
+// problem has its own descriptor and its own Scalars (dt, t, wave-speed max).
+struct ProbDesc {
+  int nx, ny, pitch, pad;
+  long long off;    // element offset of the problem's first plane in the pool
+  long long plane;  // elements between its planes
+  double rdx, rdy;
+};
+// A unit of work: one warp strip of one problem over rows [j0, jend).
+struct Unit {
+  int p, i0, j0, jend;
+};
+struct BatchDesc {
+  MeshDesc common;        // bc, limiter, riemann, gamma, beta, vec (per-problem sizes unused)
+  const ProbDesc* probs;  // device
+  const Unit* units;      // device
+  int nunits;
+  int grid;               // persistent CTAs
+};
+
 // Per-stage launch of the fused stage kernel (one Heun stage over the mesh).
 // stage 0: out = Uin - dt L(Uin)                      (predictor, Heun step 6)
 // stage 1: out = (Un + Uin)/2 - dt/2 L(Uin)           (corrector, Heun step 11),
@@ -62,6 +82,17 @@ cudaError_t launch_cons_to_prim(const MeshDesc& m, const T* U, T* rho, T* u, T* 
 template <typename T>
 cudaError_t launch_sums(const MeshDesc& m, const T* U, double* partials, int nblocks, double* out,
                         cudaStream_t s);
+
+// One persistent launch per stage over all problems of a batch; counter is
+// the stage's work counter (reset by launch_batch_begin).
+template <typename T>
+cudaError_t launch_batch_stage(int stage, const BatchDesc& b, const T* Uin, const T* Un, T* out, Scalars* sc,
+                               int* counter, cudaStream_t s);
+// Resident CTAs per SM of the batch stage kernel (for sizing the persistent grid).
+template <typename T>
+int batch_blocks_per_sm(int stage, int limiter);
+cudaError_t launch_batch_begin(Scalars* sc, int nprob, double dt_fixed, int* counters, cudaStream_t s);
+cudaError_t launch_batch_end(Scalars* sc, int nprob, cudaStream_t s);
 
 cudaError_t launch_begin_step(Scalars* sc, double dt_fixed, cudaStream_t s);
 cudaError_t launch_end_step(Scalars* sc, cudaStream_t s);

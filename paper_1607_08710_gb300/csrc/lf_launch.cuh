@@ -20,6 +20,17 @@ cudaError_t launch_stage(int stage, const MeshDesc& m, const T* Uin, const T* Un
 }
 
 template <typename T>
+cudaError_t launch_batch_stage(int stage, const BatchDesc& b, const T* Uin, const T* Un, T* out, Scalars* sc,
+                               int* counter, cudaStream_t s) {
+  return launch_batch_stage_impl<T>(stage, b, Uin, Un, out, sc, counter, s);
+}
+
+template <typename T>
+int batch_blocks_per_sm(int stage, int limiter) {
+  return batch_blocks_impl<T>(stage, limiter);
+}
+
+template <typename T>
 cudaError_t launch_wave_speed(const MeshDesc& m, const T* U, Scalars* sc, cudaStream_t s) {
   const int nb = aux_blocks((long long)m.nx * m.ny);
   if (m.dim == 1) wave_speed_kernel<T, 1><<<nb, AUX_THREADS, 0, s>>>(m, U, sc);
@@ -52,6 +63,9 @@ cudaError_t launch_sums(const MeshDesc& m, const T* U, double* partials, int nbl
   template cudaError_t launch_stage<T>(int, const MeshDesc&, const T*, const T*, T*, Scalars*,         \
                                        cudaStream_t);                                                  \
   template cudaError_t launch_wave_speed<T>(const MeshDesc&, const T*, Scalars*, cudaStream_t);        \
+  template cudaError_t launch_batch_stage<T>(int, const BatchDesc&, const T*, const T*, T*, Scalars*, int*,  \
+                                             cudaStream_t);                                            \
+  template int batch_blocks_per_sm<T>(int, int);                                                       \
   template cudaError_t launch_prim_to_cons<T>(const MeshDesc&, const T*, const T*, const T*, const T*, \
                                               long long, T*, cudaStream_t);                            \
   template cudaError_t launch_cons_to_prim<T>(const MeshDesc&, const T*, T*, T*, T*, T*, cudaStream_t); \

@@ -10,7 +10,7 @@ namespace lf {
 // or dt_fixed > 0, clipped to t_end - t; 0 once t_end is reached or after a
 // device error (the stage kernels then return at once).  Also clears the
 // wave-speed slot the coming corrector will fill.
-__global__ void begin_step_kernel(Scalars* sc, double dt_fixed) {
+__device__ __forceinline__ void begin_step_one(Scalars* sc, double dt_fixed) {
   double dt = 0.0;
   if (sc->err == 0) {
     if (dt_fixed > 0.0) {
@@ -32,12 +32,31 @@ __global__ void begin_step_kernel(Scalars* sc, double dt_fixed) {
   sc->smax[sc->parity ^ 1] = 0ull;
 }
 
-__global__ void end_step_kernel(Scalars* sc) {
+__device__ __forceinline__ void end_step_one(Scalars* sc) {
   if (sc->dt > 0.0) {
     sc->t += sc->dt;
     sc->steps += 1;
     sc->parity ^= 1;
   }
+}
+
+__global__ void begin_step_kernel(Scalars* sc, double dt_fixed) { begin_step_one(sc, dt_fixed); }
+__global__ void end_step_kernel(Scalars* sc) { end_step_one(sc); }
+
+// Batched mode: one thread per problem; thread 0 also resets the two stage
+// work counters of the coming step.
+__global__ void batch_begin_kernel(Scalars* sc, int n, double dt_fixed, int* counters) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p == 0) {
+    counters[0] = 0;
+    counters[1] = 0;
+  }
+  if (p < n) begin_step_one(sc + p, dt_fixed);
+}
+
+__global__ void batch_end_kernel(Scalars* sc, int n) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) end_step_one(sc + p);
 }
 
 __global__ void reset_scalars_kernel(Scalars* sc, double cfl) {
@@ -72,6 +91,14 @@ cudaError_t launch_begin_step(Scalars* sc, double dt_fixed, cudaStream_t s) {
 }
 cudaError_t launch_end_step(Scalars* sc, cudaStream_t s) {
   end_step_kernel<<<1, 1, 0, s>>>(sc);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_begin(Scalars* sc, int nprob, double dt_fixed, int* counters, cudaStream_t s) {
+  batch_begin_kernel<<<(nprob + 127) / 128, 128, 0, s>>>(sc, nprob, dt_fixed, counters);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_end(Scalars* sc, int nprob, cudaStream_t s) {
+  batch_end_kernel<<<(nprob + 127) / 128, 128, 0, s>>>(sc, nprob);
   return cudaGetLastError();
 }
 cudaError_t launch_reset_scalars(Scalars* sc, double cfl, cudaStream_t s) {

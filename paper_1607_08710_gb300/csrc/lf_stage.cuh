@@ -158,8 +158,8 @@ __device__ __forceinline__ void x_fluxes(const Phys<T>& P, const T q[CPL][4], T 
     for (int j = 0; j < CPL; ++j) {
       const T dplus = (j + 1 < CPL ? q[j + 1][k] : right) - q[j][k];
       const T s = limiter<T, LIM>(dminus, dplus, P.beta);
-      qL[j][k] = q[j][k] + T(0.5) * s;
-      qR[j][k] = q[j][k] - T(0.5) * s;
+      qL[j][k] = fma_(T(0.5), s, q[j][k]);
+      qR[j][k] = fma_(T(-0.5), s, q[j][k]);
       dminus = dplus;
     }
   }
@@ -190,6 +190,11 @@ __device__ __forceinline__ void publish_speed(Scalars* sc, int wpar, T smax, boo
     if (any_bad) atomicOr(&sc->err, ERR_NONPHYSICAL);
   }
 }
+
+// Cells per lane and tile height per precision (FP64 keeps one cell per lane
+// to stay clear of register spills).
+template <typename T> struct StageShape { static constexpr int CPL = 2, TY = LF_TY_F32; };
+template <> struct StageShape<double> { static constexpr int CPL = 1, TY = LF_TY_F64; };
 
 // ---------------------------------------------------------------------------
 // Asynchronous row staging.  Every row a warp reads from global memory is
@@ -315,8 +320,8 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, c
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       M.s[S1][j][k] = limiter<T, LIM>(M.q[S1][j][k] - M.q[S][j][k], M.q[S2][j][k] - M.q[S1][j][k], P.beta);
-      Lq[k] = M.q[S][j][k] + T(0.5) * M.s[S][j][k];
-      Rq[k] = M.q[S1][j][k] - T(0.5) * M.s[S1][j][k];
+      Lq[k] = fma_(T(0.5), M.s[S][j][k], M.q[S][j][k]);
+      Rq[k] = fma_(T(-0.5), M.s[S1][j][k], M.q[S1][j][k]);
     }
     lagrange_flux<T, 1>(P, Lq, Rq, M.G[S1][j]);
   }
@@ -334,7 +339,7 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, c
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const T base = STAGE == 0 ? U[j][k] : T(0.5) * (Un[j][k] + U[j][k]);
-      W[j][k] = base - cx * (Fr[j][k] - Fl[j][k]) - cy * (M.G[S1][j][k] - M.G[S][j][k]);
+      W[j][k] = fma_(-cy, M.G[S1][j][k] - M.G[S][j][k], fma_(-cx, Fr[j][k] - Fl[j][k], base));
     }
   const int off = r * m.pitch;
   if (L.vec_ok) {
@@ -363,24 +368,15 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, c
   }
 }
 
+// One warp's strip of columns [i0-2, i0-2+32*CPL) over the tile rows
+// [j0, jend): the whole y-march, from the prologue to the last row.  The
+// warp's rings start empty and are left with no copy in flight.
 // STAGE 0: out = Uin - dt L(Uin).  STAGE 1: out = (Un + Uin)/2 - dt/2 L(Uin).
-// Dynamic shared memory: STAGE_WARPS * Ring<T,CPL>::warp_bytes(STAGE).
-template <typename T, int LIM, int STAGE, int CPL, int TY>
-__global__ void __launch_bounds__(STAGE_WARPS * 32, LF_MIN_BLOCKS)
-stage2d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out, Scalars* sc) {
-  extern __shared__ __align__(16) unsigned char lf_stage_smem[];
-  const double dtd = sc->dt;
-  if (!(dtd > 0.0)) return;
-  const int wpar = sc->parity ^ 1;
-  const Phys<T> P(m);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i0 = (blockIdx.x * STAGE_WARPS + warp) * StripGeom<CPL>::OUT;
-  if (i0 >= m.nx) return;  // whole warp
+template <typename T, int LIM, int STAGE, int CPL>
+__device__ __forceinline__ void strip_tile(const Phys<T>& P, const MeshDesc& m, const T* Uin, const T* Un, T* out,
+                                           int i0, int j0, int jend, T cx, T cy, T* ring_in, int lane, T& smax,
+                                           bool& bad) {
   const LaneCols<CPL> L = lane_cols<CPL>(i0, lane, m.nx, m.bc, m.vec);
-  const int j0 = blockIdx.y * TY;
-  const int jend = min(j0 + TY, m.ny);
-  const double hs = STAGE == 0 ? 1.0 : 0.5;
-  const T cx = T(hs * dtd * m.rdx), cy = T(hs * dtd * m.rdy);
   constexpr int ROW = Ring<T, CPL>::ROW;
   StageArgs<T, STAGE, CPL> A;
 #pragma unroll
@@ -389,8 +385,8 @@ stage2d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
     A.N[k] = Un + k * m.plane;
     A.O[k] = out + k * m.plane;
   }
-  A.ring_in = reinterpret_cast<T*>(lf_stage_smem + warp * Ring<T, CPL>::warp_bytes(STAGE));
-  A.ring_un = A.ring_in + RING_IN * ROW;
+  A.ring_in = ring_in;
+  A.ring_un = ring_in + RING_IN * ROW;
   A.j0 = j0;
 
   // Prologue.  Group 0: input rows j0-2 .. j0+1.  Group 1: input row j0+2 and
@@ -404,8 +400,8 @@ stage2d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
   cp_commit();
   issue_row<T, CPL>(A.ring_in + ring_slot(j0 + 2, j0, RING_IN) * ROW, A.P, L, map_row(j0 + 2, m.ny, m.bc) * m.pitch,
                     lane);
-  if (STAGE == 1 && L.any_out) issue_out_cells<T, CPL>(A.ring_un + ring_slot(j0, j0, RING_UN) * ROW, A.N, L,
-                                                      j0 * m.pitch, lane);
+  if (STAGE == 1 && L.any_out)
+    issue_out_cells<T, CPL>(A.ring_un + ring_slot(j0, j0, RING_UN) * ROW, A.N, L, j0 * m.pitch, lane);
   cp_commit();
   cp_wait<1>();
   March<T, CPL> M;
@@ -426,8 +422,8 @@ stage2d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
       for (int k = 0; k < 4; ++k) {
         M.s[2][j][k] = limiter<T, LIM>(M.q[2][j][k] - qm2[j][k], M.q[0][j][k] - M.q[2][j][k], P.beta);
         M.s[0][j][k] = limiter<T, LIM>(M.q[0][j][k] - M.q[2][j][k], M.q[1][j][k] - M.q[0][j][k], P.beta);
-        Lq[k] = M.q[2][j][k] + T(0.5) * M.s[2][j][k];
-        Rq[k] = M.q[0][j][k] - T(0.5) * M.s[0][j][k];
+        Lq[k] = fma_(T(0.5), M.s[2][j][k], M.q[2][j][k]);
+        Rq[k] = fma_(T(-0.5), M.s[0][j][k], M.q[0][j][k]);
       }
       lagrange_flux<T, 1>(P, Lq, Rq, M.G[0][j]);
     }
@@ -440,8 +436,6 @@ stage2d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
   }
   cp_commit();
 
-  T smax = T(0);
-  bool bad = false;
   for (int r = j0;;) {
     march_row<T, LIM, STAGE, CPL, 0>(P, m, A, L, M, lane, r, jend, cx, cy, smax, bad);
     if (++r >= jend) break;
@@ -451,7 +445,92 @@ stage2d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
     if (++r >= jend) break;
   }
   cp_wait_all();
+}
+
+// One mesh: a 2D grid of (strips / STAGE_WARPS) x (row tiles) CTAs.
+// Dynamic shared memory: STAGE_WARPS * Ring<T,CPL>::warp_bytes(STAGE).
+template <typename T, int LIM, int STAGE, int CPL, int TY>
+__global__ void __launch_bounds__(STAGE_WARPS * 32, LF_MIN_BLOCKS)
+stage2d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out, Scalars* sc) {
+  extern __shared__ __align__(16) unsigned char lf_stage_smem[];
+  const double dtd = sc->dt;
+  if (!(dtd > 0.0)) return;
+  const int wpar = sc->parity ^ 1;
+  const Phys<T> P(m);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = (blockIdx.x * STAGE_WARPS + warp) * StripGeom<CPL>::OUT;
+  if (i0 >= m.nx) return;  // whole warp
+  const int j0 = blockIdx.y * TY;
+  const int jend = min(j0 + TY, m.ny);
+  const double hs = STAGE == 0 ? 1.0 : 0.5;
+  const T cx = T(hs * dtd * m.rdx), cy = T(hs * dtd * m.rdy);
+  T* ring = reinterpret_cast<T*>(lf_stage_smem + warp * Ring<T, CPL>::warp_bytes(STAGE));
+  T smax = T(0);
+  bool bad = false;
+  strip_tile<T, LIM, STAGE, CPL>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring, lane, smax, bad);
   if (STAGE == 1) publish_speed(sc, wpar, smax, bad);
+}
+
+// Many meshes: a persistent grid whose warps pull work units (problem, strip,
+// row tile) from an atomic counter until the list is exhausted.  Each problem
+// uses its own dt, and its corrector units feed its own wave-speed maximum.
+#ifndef LF_BATCH_MIN_BLOCKS
+#define LF_BATCH_MIN_BLOCKS 4
+#endif
+template <typename T, int LIM, int STAGE, int CPL>
+__global__ void __launch_bounds__(STAGE_WARPS * 32, LF_BATCH_MIN_BLOCKS)
+batch_stage_kernel(const BatchDesc b, const T* Uin, const T* Un, T* out, Scalars* sc, int* counter) {
+  extern __shared__ __align__(16) unsigned char lf_stage_smem[];
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* ring = reinterpret_cast<T*>(lf_stage_smem + warp * Ring<T, CPL>::warp_bytes(STAGE));
+  for (;;) {
+    int u = 0;
+    if (lane == 0) u = atomicAdd(counter, 1);
+    u = __shfl_sync(FULL, u, 0);
+    if (u >= b.nunits) break;
+    const Unit un = b.units[u];
+    const ProbDesc pd = b.probs[un.p];
+    Scalars* scp = sc + un.p;
+    const double dtd = scp->dt;
+    if (!(dtd > 0.0)) continue;  // problem finished (t_end reached) or flagged
+    MeshDesc m = b.common;
+    m.nx = pd.nx;
+    m.ny = pd.ny;
+    m.pitch = pd.pitch;
+    m.plane = pd.plane;
+    m.rdx = pd.rdx;
+    m.rdy = pd.rdy;
+    const Phys<T> P(m);
+    const double hs = STAGE == 0 ? 1.0 : 0.5;
+    const T cx = T(hs * dtd * m.rdx), cy = T(hs * dtd * m.rdy);
+    T smax = T(0);
+    bool bad = false;
+    strip_tile<T, LIM, STAGE, CPL>(P, m, Uin + pd.off, Un + pd.off, out + pd.off, un.i0, un.j0, un.jend, cx, cy,
+                                   ring, lane, smax, bad);
+    if (STAGE == 1) publish_speed(scp, scp->parity ^ 1, smax, bad);
+  }
+}
+
+template <typename T, int LIM>
+cudaError_t launch_batch_stage_lim(int stage, const BatchDesc& b, const T* Uin, const T* Un, T* out, Scalars* sc,
+                                   int* counter, cudaStream_t s) {
+  constexpr int CPL = StageShape<T>::CPL;
+  const size_t smem = STAGE_WARPS * Ring<T, CPL>::warp_bytes(stage);
+  if (stage == 0) batch_stage_kernel<T, LIM, 0, CPL><<<b.grid, STAGE_WARPS * 32, smem, s>>>(b, Uin, Un, out, sc, counter);
+  else batch_stage_kernel<T, LIM, 1, CPL><<<b.grid, STAGE_WARPS * 32, smem, s>>>(b, Uin, Un, out, sc, counter);
+  return cudaGetLastError();
+}
+
+template <typename T, int LIM>
+int batch_blocks_lim(int stage) {
+  constexpr int CPL = StageShape<T>::CPL;
+  const size_t smem = STAGE_WARPS * Ring<T, CPL>::warp_bytes(stage);
+  int nb = 0;
+  cudaError_t e = stage == 0
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_stage_kernel<T, LIM, 0, CPL>, STAGE_WARPS * 32, smem)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_stage_kernel<T, LIM, 1, CPL>, STAGE_WARPS * 32, smem);
+  return e == cudaSuccess ? nb : 0;
 }
 
 // 1D: one row, no y-terms.
@@ -483,7 +562,7 @@ stage1d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const T base = STAGE == 0 ? U[j][k] : T(0.5) * (Un[k * m.plane + c] + U[j][k]);
-      W[k] = base - cx * (Fr[j][k] - Fl[j][k]);
+      W[k] = fma_(-cx, Fr[j][k] - Fl[j][k], base);
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) out[k * m.plane + c] = W[k];
@@ -495,11 +574,6 @@ stage1d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
   }
   if (STAGE == 1) publish_speed(sc, wpar, smax, bad);
 }
-
-// Cells per lane and tile height per precision (FP64 keeps one cell per lane
-// to stay clear of register spills).
-template <typename T> struct StageShape { static constexpr int CPL = 2, TY = LF_TY_F32; };
-template <> struct StageShape<double> { static constexpr int CPL = 1, TY = LF_TY_F64; };
 
 template <typename T, int LIM>
 cudaError_t launch_stage_lim(int stage, const MeshDesc& m, const T* Uin, const T* Un, T* out, Scalars* sc,
@@ -518,6 +592,25 @@ cudaError_t launch_stage_lim(int stage, const MeshDesc& m, const T* Uin, const T
     else stage2d_kernel<T, LIM, 1, CPL, TY><<<grid, block, smem, s>>>(m, Uin, Un, out, sc);
   }
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_batch_stage_impl(int stage, const BatchDesc& b, const T* Uin, const T* Un, T* out, Scalars* sc,
+                                    int* counter, cudaStream_t s) {
+  switch (b.common.limiter) {
+    case LIM_MINMOD: return launch_batch_stage_lim<T, LIM_MINMOD>(stage, b, Uin, Un, out, sc, counter, s);
+    case LIM_SWEBY: return launch_batch_stage_lim<T, LIM_SWEBY>(stage, b, Uin, Un, out, sc, counter, s);
+    default: return launch_batch_stage_lim<T, LIM_VANLEER>(stage, b, Uin, Un, out, sc, counter, s);
+  }
+}
+
+template <typename T>
+int batch_blocks_impl(int stage, int limiter) {
+  switch (limiter) {
+    case LIM_MINMOD: return batch_blocks_lim<T, LIM_MINMOD>(stage);
+    case LIM_SWEBY: return batch_blocks_lim<T, LIM_SWEBY>(stage);
+    default: return batch_blocks_lim<T, LIM_VANLEER>(stage);
+  }
 }
 
 template <typename T>

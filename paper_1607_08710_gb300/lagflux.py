@@ -64,6 +64,15 @@ SIGNATURES = {
     "lf_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lf_profile_read": (ctypes.c_int, [_vp, _P(_d), _P(_i64)]),
     "lf_step_noalloc": (ctypes.c_int, [_P(lf_config), _vp, _vp, _d, _P(_d), _vp]),
+    "lf_batch_init": (ctypes.c_int, [_P(lf_config), _i32, _vp, _P(_vp)]),
+    "lf_batch_destroy": (None, [_vp]),
+    "lf_batch_set_primitive": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, ctypes.c_int]),
+    "lf_batch_get_state": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, ctypes.c_int]),
+    "lf_batch_run": (ctypes.c_int, [_vp, _i32, _i32]),
+    "lf_batch_autotune": (ctypes.c_int, [_vp, _i32, _P(_i32)]),
+    "lf_batch_set_rows": (ctypes.c_int, [_vp, _i32]),
+    "lf_batch_get_times": (ctypes.c_int, [_vp, _P(_d), _P(_i64)]),
+    "lf_batch_last_error": (ctypes.c_char_p, [_vp]),
     "lf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lf_last_error": (ctypes.c_char_p, [_vp]),
 }
@@ -267,3 +276,84 @@ class LagrangeFlux:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class LagrangeFluxBatch:
+    """Many independent 2D meshes advanced together (one persistent launch per stage)."""
+
+    def __init__(self, cfgs, stream=None):
+        if not cfgs:
+            raise ValueError("need at least one problem")
+        self.cfgs = list(cfgs)
+        if stream is None:
+            try:
+                import torch
+
+                stream = torch.cuda.current_stream(cfgs[0].device).cuda_stream if torch.cuda.is_available() else 0
+            except ImportError:
+                stream = 0
+        arr = (lf_config * len(self.cfgs))(*[c.to_c() for c in self.cfgs])
+        h = ctypes.c_void_p()
+        st = _lib.lf_batch_init(arr, len(self.cfgs), ctypes.c_void_p(stream), ctypes.byref(h))
+        if st != LF_OK:
+            raise LagrangeFluxError(st, _lib.lf_batch_last_error(None).decode())
+        self._h = h
+
+    def _check(self, st: int):
+        if st != LF_OK:
+            raise LagrangeFluxError(st, _lib.lf_batch_last_error(self._h).decode())
+
+    def _planes(self, p, planes):
+        c = self.cfgs[p]
+        n = c.nx * c.ny
+        ptrs, kinds = [], set()
+        for a in planes:
+            ptr, k = _ptr_and_kind(a)
+            if int(np.prod(a.shape)) != n:
+                raise ValueError(f"problem {p}: plane has {int(np.prod(a.shape))} elements, expected {n}")
+            ptrs.append(ptr)
+            kinds.add(k)
+        if len(kinds) != 1:
+            raise ValueError("all planes must be on the same side (all host or all device)")
+        return ptrs, kinds.pop()
+
+    def set_primitive(self, p, rho, u, v, pr):
+        ptrs, k = self._planes(p, [rho, u, v, pr])
+        self._check(_lib.lf_batch_set_primitive(self._h, p, *ptrs, k))
+
+    def get_state(self, p, out=None):
+        c = self.cfgs[p]
+        if out is None:
+            out = np.empty((4, c.ny, c.nx), dtype=c.np_dtype)
+        ptrs, k = self._planes(p, [out[0], out[1], out[2], out[3]])
+        self._check(_lib.lf_batch_get_state(self._h, p, *ptrs, k))
+        return out
+
+    def run(self, nsteps: int, use_graph: bool = True):
+        self._check(_lib.lf_batch_run(self._h, int(nsteps), 1 if use_graph else 0))
+
+    def autotune(self, trial_steps: int = 3) -> int:
+        rows = ctypes.c_int32()
+        self._check(_lib.lf_batch_autotune(self._h, int(trial_steps), ctypes.byref(rows)))
+        return rows.value
+
+    def set_rows(self, rows: int):
+        self._check(_lib.lf_batch_set_rows(self._h, int(rows)))
+
+    def times(self):
+        n = len(self.cfgs)
+        t = (ctypes.c_double * n)()
+        s = (ctypes.c_int64 * n)()
+        self._check(_lib.lf_batch_get_times(self._h, t, s))
+        return np.array(t[:]), np.array(s[:])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
