@@ -147,6 +147,31 @@ lf_status lf_profile_enable(lf_ctx* ctx, int enable);
 lf_status lf_profile_read(lf_ctx* ctx, double ms[2], int64_t launches[2]);
 
 /* ------------------------------------------------------------------------
+ * Discrete adjoint of the Heun/RK2 step (Sec. 4) with the dt sequence frozen,
+ * for 2D meshes and the eqs. 13-14 interface solver.  Limiter branches are
+ * differentiated piecewise; at non-smooth points max/min take the first
+ * argument on ties, the limiter has zero derivative where ab <= 0, and the
+ * upwind side follows the sign of u*.
+ * ------------------------------------------------------------------------ */
+
+/* Runs nsteps CFL steps from the context's current state (as lf_step does),
+ * keeping a checkpoint of the state every ceil(sqrt(nsteps)) steps and the
+ * dt of every step; the context ends at the final state U(T).  Allocates the
+ * checkpoints (ceil(nsteps / ceil(sqrt(nsteps))) states), one segment of
+ * recomputed states and adjoint work buffers; they are kept for reuse until
+ * lf_destroy.  dts_out (nullable, nsteps doubles) receives the dt sequence.
+ * Synchronises. */
+lf_status lf_adjoint_forward(lf_ctx* ctx, int32_t nsteps, double* dts_out);
+
+/* Given lambda_T = dJ/dU(T) (device, 4 dense planes of the configured
+ * precision, conservative variables, x fastest), computes dJ/dU(0) of the
+ * last recorded forward run by sweeping its checkpoints backwards.
+ * grad_U0 (nullable): device, 4 dense planes of dJ/dU(0).
+ * grad_q0 (nullable): device, 4 dense planes of dJ/d(rho, u, v, p) at t = 0.
+ * The context's state (U(T)) is left unchanged.  Synchronises. */
+lf_status lf_adjoint_backward(lf_ctx* ctx, const void* lambda_T, void* grad_U0, void* grad_q0);
+
+/* ------------------------------------------------------------------------
  * Batched mode: many independent 2D meshes of uneven sizes advanced together
  * by the same Heun/RK2 Lagrange-flux step (Sec. 4), each problem with its own
  * CFL time step, time and step count.  One persistent kernel launch per

@@ -11,34 +11,13 @@
 #include <vector>
 
 #include "../../include/lagflux.h"
-#include "lf_internal.h"
-
-struct lf_ctx {
-  lf_config cfg;
-  lf::MeshDesc mesh;
-  cudaStream_t stream = nullptr;
-  size_t elem = 8;            // bytes per element
-  void* U = nullptr;          // current state, 4 pitched planes
-  void* Ustar = nullptr;      // Heun predictor state, 4 pitched planes
-  void* staging = nullptr;    // dense 4 planes for host primitive transfers (lazy)
-  lf::Scalars* sc = nullptr;  // device scalars
-  lf::Scalars* hsc = nullptr; // pinned host mirror for read-back
-  double* partials = nullptr; // conservation-sum partials
-  double* dsums = nullptr;    // 4 device doubles
-  bool has_state = false;
-  // stage tracing: event pairs recorded around each stage launch
-  bool profiling = false;
-  std::vector<cudaEvent_t> ev_pool;
-  std::vector<int> ev_stage;   // stage of each recorded pair
-  size_t ev_used = 0;          // pairs recorded
-  char last_error[512] = {0};
-};
+#include "lf_host.h"
 
 namespace {
-
 char g_init_error[512] = "";
+}  // namespace
 
-void set_err(lf_ctx* c, const char* fmt, ...) {
+void lf::set_err(lf_ctx* c, const char* fmt, ...) {
   char* dst = c ? c->last_error : g_init_error;
   va_list ap;
   va_start(ap, fmt);
@@ -46,31 +25,16 @@ void set_err(lf_ctx* c, const char* fmt, ...) {
   va_end(ap);
 }
 
-// Makes the context's device current for the duration of a call and puts
-// the caller's device back afterwards.
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = true;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
-lf_status cuda_fail(lf_ctx* c, cudaError_t e, const char* what) {
+lf_status lf::cuda_fail(lf_ctx* c, cudaError_t e, const char* what) {
   set_err(c, "%s: %s", what, cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? LF_ERR_OOM : LF_ERR_CUDA;
 }
 
-#define LF_CUDA(ctx, call)                                  \
-  do {                                                      \
-    cudaError_t e_ = (call);                                \
-    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
-  } while (0)
+using lf::cuda_fail;
+using lf::DeviceGuard;
+using lf::set_err;
+
+namespace {
 
 const char* validate(const lf_config* c) {
   if (!c) return "config is NULL";
@@ -124,8 +88,10 @@ lf_status dispatch_stage(lf_ctx* c, int stage) {
   return LF_OK;
 }
 
+}  // namespace
+
 // begin (dt) -> predictor -> corrector -> end (t, steps, parity)
-lf_status enqueue_step(lf_ctx* c, double dt_fixed) {
+lf_status lf::enqueue_step(lf_ctx* c, double dt_fixed) {
   LF_CUDA(c, lf::launch_begin_step(c->sc, dt_fixed, c->stream));
   for (int stage = 0; stage < 2; ++stage) {
     lf_status st = c->elem == 8 ? dispatch_stage<double>(c, stage) : dispatch_stage<float>(c, stage);
@@ -135,13 +101,13 @@ lf_status enqueue_step(lf_ctx* c, double dt_fixed) {
   return LF_OK;
 }
 
-lf_status read_scalars(lf_ctx* c) {
+lf_status lf::read_scalars(lf_ctx* c) {
   LF_CUDA(c, cudaMemcpyAsync(c->hsc, c->sc, sizeof(lf::Scalars), cudaMemcpyDeviceToHost, c->stream));
   LF_CUDA(c, cudaStreamSynchronize(c->stream));
   return LF_OK;
 }
 
-lf_status device_error_status(lf_ctx* c) {
+lf_status lf::device_error_status(lf_ctx* c) {
   if (c->hsc->err & lf::ERR_NONPHYSICAL) {
     set_err(c, "non-positive density or pressure (or NaN) in the state");
     return LF_ERR_NONPHYSICAL;
@@ -152,6 +118,12 @@ lf_status device_error_status(lf_ctx* c) {
   }
   return LF_OK;
 }
+
+using lf::device_error_status;
+using lf::enqueue_step;
+using lf::read_scalars;
+
+namespace {
 
 // Fresh time loop on the state just written into c->U.
 lf_status restart_clock(lf_ctx* c) {
@@ -231,6 +203,7 @@ void lf_destroy(lf_ctx* c) {
     cudaFree(c->dsums);
     cudaFreeHost(c->hsc);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    lf::free_adjoint(c);
   }
   delete c;
 }

@@ -1,0 +1,80 @@
+// Host-side internals shared by the C-ABI translation units: the context
+// structure and small helpers.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/lagflux.h"
+#include "lf_internal.h"
+
+struct lf_ctx {
+  lf_config cfg;
+  lf::MeshDesc mesh;
+  cudaStream_t stream = nullptr;
+  size_t elem = 8;            // bytes per element
+  void* U = nullptr;          // current state, 4 pitched planes
+  void* Ustar = nullptr;      // Heun predictor state, 4 pitched planes
+  void* staging = nullptr;    // dense 4 planes for host primitive transfers (lazy)
+  lf::Scalars* sc = nullptr;  // device scalars
+  lf::Scalars* hsc = nullptr; // pinned host mirror for read-back
+  double* partials = nullptr; // conservation-sum partials
+  double* dsums = nullptr;    // 4 device doubles
+  bool has_state = false;
+  // stage tracing: event pairs recorded around each stage launch
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_stage;   // stage of each recorded pair
+  size_t ev_used = 0;          // pairs recorded
+  // discrete adjoint (lf_adjoint_*): checkpoints of the forward run and work buffers
+  struct Adjoint {
+    int nsteps = 0;            // steps of the recorded forward run (0: none)
+    int seg = 0;               // checkpoint interval
+    std::vector<double> dts;   // frozen dt sequence
+    size_t state_elems = 0;    // elements of one state (4 planes)
+    size_t ck_cap = 0, seg_cap = 0, face_cap = 0, dts_cap = 0;
+    void* ck = nullptr;        // checkpoints: ceil(nsteps / seg) states
+    void* segbuf = nullptr;    // recomputed states of one segment
+    void* lam = nullptr;       // cotangent of the state
+    void* lamstar = nullptr;   // cotangent of the predictor state
+    void* fx = nullptr;        // face-state cotangents, x-faces
+    void* fy = nullptr;        // face-state cotangents, y-faces
+    double* dts_dev = nullptr; // dt of each forward step, recorded on the device
+    lf::Scalars* sc = nullptr; // scalars of the recomputation
+  } adj;
+  char last_error[512] = {0};
+};
+
+namespace lf {
+
+void set_err(lf_ctx* c, const char* fmt, ...);
+lf_status cuda_fail(lf_ctx* c, cudaError_t e, const char* what);
+// One Heun step on the context (dt_fixed > 0: that dt; else the CFL dt).
+lf_status enqueue_step(lf_ctx* c, double dt_fixed);
+lf_status read_scalars(lf_ctx* c);
+lf_status device_error_status(lf_ctx* c);
+void free_adjoint(lf_ctx* c);
+
+// Makes the context's device current for the duration of a call and puts
+// the caller's device back afterwards.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace lf
+
+#define LF_CUDA(ctx, call)                                      \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return lf::cuda_fail(ctx, e_, #call); \
+  } while (0)

@@ -94,6 +94,18 @@ int batch_blocks_per_sm(int stage, int limiter);
 cudaError_t launch_batch_begin(Scalars* sc, int nprob, double dt_fixed, int* counters, cudaStream_t s);
 cudaError_t launch_batch_end(Scalars* sc, int nprob, cudaStream_t s);
 
+// Discrete adjoint (lf_adjoint.cuh).  Face pass: cotangents of the face
+// states of every x-face (dir 0) or y-face (dir 1) for the cell cotangent mu.
+template <typename T>
+cudaError_t launch_face_vjp(const MeshDesc& m, int dir, const T* U, const T* mu, T* Fq, cudaStream_t s);
+// Cell pass: out = alpha X + beta Y + c (dD/dU)^T mu (X, Y nullable).
+template <typename T>
+cudaError_t launch_cell_vjp(const MeshDesc& m, const T* U, const T* Fx, const T* Fy, const T* X, double alpha,
+                            const T* Y, double beta, double c, T* out, cudaStream_t s);
+// Gradient with respect to the primitive initial fields (dense planes).
+template <typename T>
+cudaError_t launch_grad_prim(const MeshDesc& m, const T* U0, const T* lam, T* gq, cudaStream_t s);
+
 cudaError_t launch_begin_step(Scalars* sc, double dt_fixed, cudaStream_t s);
 cudaError_t launch_end_step(Scalars* sc, cudaStream_t s);
 cudaError_t launch_reset_scalars(Scalars* sc, double cfl, cudaStream_t s);

@@ -2,6 +2,7 @@
 // unit per precision, which instantiates them with LF_INSTANTIATE_LAUNCHERS.
 #pragma once
 
+#include "lf_adjoint.cuh"
 #include "lf_aux.cuh"
 #include "lf_stage.cuh"
 
@@ -59,6 +60,47 @@ cudaError_t launch_sums(const MeshDesc& m, const T* U, double* partials, int nbl
   return cudaGetLastError();
 }
 
+template <typename T, int LIM>
+cudaError_t launch_face_vjp_lim(const MeshDesc& m, int dir, const T* U, const T* mu, T* Fq, cudaStream_t s) {
+  const long long nfaces = dir == 0 ? (long long)(m.nx + 1) * m.ny : (long long)(m.ny + 1) * m.nx;
+  const int nb = aux_blocks(nfaces);
+  if (dir == 0) face_vjp_kernel<T, LIM, 0><<<nb, AUX_THREADS, 0, s>>>(m, U, mu, Fq);
+  else face_vjp_kernel<T, LIM, 1><<<nb, AUX_THREADS, 0, s>>>(m, U, mu, Fq);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_face_vjp(const MeshDesc& m, int dir, const T* U, const T* mu, T* Fq, cudaStream_t s) {
+  switch (m.limiter) {
+    case LIM_MINMOD: return launch_face_vjp_lim<T, LIM_MINMOD>(m, dir, U, mu, Fq, s);
+    case LIM_SWEBY: return launch_face_vjp_lim<T, LIM_SWEBY>(m, dir, U, mu, Fq, s);
+    default: return launch_face_vjp_lim<T, LIM_VANLEER>(m, dir, U, mu, Fq, s);
+  }
+}
+
+template <typename T>
+cudaError_t launch_cell_vjp(const MeshDesc& m, const T* U, const T* Fx, const T* Fy, const T* X, double alpha,
+                            const T* Y, double beta, double c, T* out, cudaStream_t s) {
+  const int nb = aux_blocks((long long)m.nx * m.ny);
+  switch (m.limiter) {
+    case LIM_MINMOD:
+      cell_vjp_kernel<T, LIM_MINMOD><<<nb, AUX_THREADS, 0, s>>>(m, U, Fx, Fy, X, T(alpha), Y, T(beta), T(c), out);
+      break;
+    case LIM_SWEBY:
+      cell_vjp_kernel<T, LIM_SWEBY><<<nb, AUX_THREADS, 0, s>>>(m, U, Fx, Fy, X, T(alpha), Y, T(beta), T(c), out);
+      break;
+    default:
+      cell_vjp_kernel<T, LIM_VANLEER><<<nb, AUX_THREADS, 0, s>>>(m, U, Fx, Fy, X, T(alpha), Y, T(beta), T(c), out);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_grad_prim(const MeshDesc& m, const T* U0, const T* lam, T* gq, cudaStream_t s) {
+  grad_prim_kernel<T><<<aux_blocks((long long)m.nx * m.ny), AUX_THREADS, 0, s>>>(m, U0, lam, gq);
+  return cudaGetLastError();
+}
+
 #define LF_INSTANTIATE_LAUNCHERS(T)                                                                    \
   template cudaError_t launch_stage<T>(int, const MeshDesc&, const T*, const T*, T*, Scalars*,         \
                                        cudaStream_t);                                                  \
@@ -69,6 +111,10 @@ cudaError_t launch_sums(const MeshDesc& m, const T* U, double* partials, int nbl
   template cudaError_t launch_prim_to_cons<T>(const MeshDesc&, const T*, const T*, const T*, const T*, \
                                               long long, T*, cudaStream_t);                            \
   template cudaError_t launch_cons_to_prim<T>(const MeshDesc&, const T*, T*, T*, T*, T*, cudaStream_t); \
-  template cudaError_t launch_sums<T>(const MeshDesc&, const T*, double*, int, double*, cudaStream_t);
+  template cudaError_t launch_sums<T>(const MeshDesc&, const T*, double*, int, double*, cudaStream_t);      \
+  template cudaError_t launch_face_vjp<T>(const MeshDesc&, int, const T*, const T*, T*, cudaStream_t);        \
+  template cudaError_t launch_cell_vjp<T>(const MeshDesc&, const T*, const T*, const T*, const T*, double,    \
+                                          const T*, double, double, T*, cudaStream_t);                      \
+  template cudaError_t launch_grad_prim<T>(const MeshDesc&, const T*, const T*, T*, cudaStream_t);
 
 }  // namespace lf

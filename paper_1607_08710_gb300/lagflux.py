@@ -64,6 +64,8 @@ SIGNATURES = {
     "lf_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lf_profile_read": (ctypes.c_int, [_vp, _P(_d), _P(_i64)]),
     "lf_step_noalloc": (ctypes.c_int, [_P(lf_config), _vp, _vp, _d, _P(_d), _vp]),
+    "lf_adjoint_forward": (ctypes.c_int, [_vp, _i32, _P(_d)]),
+    "lf_adjoint_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "lf_batch_init": (ctypes.c_int, [_P(lf_config), _i32, _vp, _P(_vp)]),
     "lf_batch_destroy": (None, [_vp]),
     "lf_batch_set_primitive": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, ctypes.c_int]),
@@ -260,6 +262,24 @@ class LagrangeFlux:
     def sync(self):
         self._check(_lib.lf_sync(self._h))
 
+    # -- discrete adjoint ------------------------------------------------
+    def adjoint_forward(self, nsteps: int) -> np.ndarray:
+        """nsteps CFL steps with sqrt(N) checkpoints; returns the frozen dt sequence."""
+        dts = np.zeros(nsteps)
+        self._check(_lib.lf_adjoint_forward(self._h, int(nsteps), dts.ctypes.data_as(_P(_d))))
+        return dts
+
+    def adjoint_backward(self, lambda_T, grad_U0=None, grad_q0=None):
+        """lambda_T: (4, ny, nx) device tensor dJ/dU(T).  Fills the given device
+        tensors with dJ/dU(0) and/or dJ/d(rho, u, v, p)(0)."""
+        for a in (lambda_T, grad_U0, grad_q0):
+            if a is not None:
+                if not getattr(a, "is_cuda", False) or not a.is_contiguous():
+                    raise ValueError("adjoint buffers must be contiguous device tensors")
+                self._check_dtype(a)
+        p = lambda a: None if a is None else a.data_ptr()
+        self._check(_lib.lf_adjoint_backward(self._h, p(lambda_T), p(grad_U0), p(grad_q0)))
+
     def close(self):
         if getattr(self, "_h", None):
             _lib.lf_destroy(self._h)
@@ -357,3 +377,38 @@ class LagrangeFluxBatch:
             self.close()
         except Exception:
             pass
+
+
+def _autograd_function():
+    import torch
+
+    class LagrangeFluxRun(torch.autograd.Function):
+        """(rho0, u0, v0, p0) -> conservative state after `nsteps` CFL steps.
+
+        The forward records the dt sequence and sqrt(N) checkpoints; the
+        backward is the discrete adjoint with that dt sequence frozen."""
+
+        @staticmethod
+        def forward(ctx, rho0, u0, v0, p0, solver, nsteps):
+            solver.set_primitive(rho0.contiguous(), u0.contiguous(), v0.contiguous(), p0.contiguous())
+            solver.adjoint_forward(nsteps)
+            c = solver.cfg
+            U = torch.empty((4, c.ny, c.nx), dtype=rho0.dtype, device=rho0.device)
+            solver.get_state(U)
+            ctx.solver = solver
+            return U
+
+        @staticmethod
+        def backward(ctx, gU):
+            s = ctx.solver
+            gq = torch.empty_like(gU)
+            s.adjoint_backward(gU.contiguous(), grad_q0=gq)
+            return gq[0], gq[1], gq[2], gq[3], None, None
+
+    return LagrangeFluxRun
+
+
+def run_differentiable(solver: "LagrangeFlux", rho0, u0, v0, p0, nsteps: int):
+    """Differentiable run: returns the (4, ny, nx) conservative state after
+    nsteps steps; gradients flow back to the primitive initial fields."""
+    return _autograd_function().apply(rho0, u0, v0, p0, solver, nsteps)
