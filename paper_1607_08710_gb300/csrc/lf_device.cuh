@@ -65,18 +65,21 @@ __device__ __forceinline__ void to_prim(const Phys<T>& P, const T U[4], T q[4]) 
   q[3] = P.gm1 * fma_(T(-0.5), fma_(U[1], u, U[2] * v), U[3]);
 }
 
-// Eq. (sweby) for LIM_MINMOD / LIM_SWEBY, and van Leer's limiter.
+// Half of the limited slope, phi(a,b)/2, so that the face states are
+// q +/- limiter_half: eq. (sweby) for LIM_MINMOD / LIM_SWEBY, and van Leer's
+// limiter (ab>0) 2ab/(a+b).  (Halving is exact in binary arithmetic, so this
+// equals 0.5 * phi bit for bit.)
 template <typename T, int LIM>
-__device__ __forceinline__ T limiter(T a, T b, T beta) {
+__device__ __forceinline__ T limiter_half(T a, T b, T beta) {
   T ab = a * b;
   if (LIM == LIM_VANLEER) {
-    return ab > T(0) ? Ar<T>::div(T(2) * ab, a + b) : T(0);
+    return ab > T(0) ? Ar<T>::div(ab, a + b) : T(0);
   } else {
     T aa = fabs(a), bb = fabs(b);
     T m;
     if (LIM == LIM_MINMOD) m = fmin(aa, bb);
     else m = fmax(fmin(aa, beta * bb), fmin(beta * aa, bb));
-    return ab > T(0) ? copysign(m, a) : T(0);
+    return ab > T(0) ? copysign(T(0.5) * m, a) : T(0);
   }
 }
 
@@ -91,13 +94,17 @@ __device__ __forceinline__ void lagrange_flux(const Phys<T>& P, const T qL[4], c
   T pstar, ustar;
   if (P.riemann == RIEMANN_MAXC) {
     // a = max(c_L, c_R) with c_k^2 = gamma p_k / rho_k; the larger c is the
-    // larger c^2, so only one square root is needed.
+    // larger c^2, so only one square root is needed.  With the weight
+    // w = rho_L / (rho_L + rho_R), eqs. (13)-(14) read
+    //   p* = p_L + w (p_R - p_L) - rho_R w a (u_R - u_L)
+    //   u* = u_R - w (u_R - u_L) - (p_R - p_L) / ((rho_L + rho_R) a).
     T a2 = P.gamma * fmax(Ar<T>::div(pL, rL), Ar<T>::div(pR, rR));
     T a, ia;
     Ar<T>::sqrt_and_rsqrt(a2, a, ia);
-    T irs = Ar<T>::rcp(rL + rR);
-    pstar = fma_(-(rL * rR * irs * a), unR - unL, fma_(rR, pL, rL * pR) * irs);
-    ustar = fma_(-((pR - pL) * irs), ia, fma_(rL, unL, rR * unR) * irs);
+    const T irs = Ar<T>::rcp(rL + rR);
+    const T w = rL * irs, dp = pR - pL, du = unR - unL;
+    pstar = fma_(-(rR * w * a), du, fma_(w, dp, pL));
+    ustar = fma_(-dp, irs * ia, fma_(-w, du, unR));
   } else {
     // acoustic solver with Z_k = rho_k c_k
     T ZL = rL * Ar<T>::sqrt_(P.gamma * Ar<T>::div(pL, rL));
@@ -124,10 +131,11 @@ __device__ __forceinline__ void lagrange_flux(const Phys<T>& P, const T qL[4], c
 // positivity (rho > 0 and p > 0; false for NaN).
 template <typename T, int DIM>
 __device__ __forceinline__ T cell_speed(const Phys<T>& P, const T U[4], bool& ok) {
-  T q[4];
-  to_prim(P, U, q);
+  const T ir = Ar<T>::rcp(U[0]);
+  const T u = U[1] * ir, v = U[2] * ir;
+  T q[4] = {U[0], u, v, P.gm1 * fma_(T(-0.5), fma_(U[1], u, U[2] * v), U[3])};
   ok = (q[0] > T(0)) && (q[3] > T(0));
-  T c = Ar<T>::sqrt_(P.gamma * Ar<T>::div(q[3], q[0]));
+  T c = Ar<T>::sqrt_(P.gamma * q[3] * ir);
   T s = (fabs(q[1]) + c) * P.rdx;
   if (DIM == 2) s = fma_(fabs(q[2]) + c, P.rdy, s);
   return s;

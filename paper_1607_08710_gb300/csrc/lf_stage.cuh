@@ -31,7 +31,7 @@ namespace lf {
 // Launch shape; the defaults were chosen by timing on GB300 and can be
 // overridden at build time for tuning sweeps.
 #ifndef LF_STAGE_WARPS
-#define LF_STAGE_WARPS 4
+#define LF_STAGE_WARPS 1
 #endif
 #ifndef LF_TY_F32
 #define LF_TY_F32 64
@@ -39,8 +39,11 @@ namespace lf {
 #ifndef LF_TY_F64
 #define LF_TY_F64 64
 #endif
-#ifndef LF_MIN_BLOCKS
-#define LF_MIN_BLOCKS 1
+#ifndef LF_MIN_BLOCKS0
+#define LF_MIN_BLOCKS0 18
+#endif
+#ifndef LF_MIN_BLOCKS1
+#define LF_MIN_BLOCKS1 16
 #endif
 constexpr int STAGE_WARPS = LF_STAGE_WARPS;  // warps per CTA, side by side in x
 
@@ -157,9 +160,9 @@ __device__ __forceinline__ void x_fluxes(const Phys<T>& P, const T q[CPL][4], T 
 #pragma unroll
     for (int j = 0; j < CPL; ++j) {
       const T dplus = (j + 1 < CPL ? q[j + 1][k] : right) - q[j][k];
-      const T s = limiter<T, LIM>(dminus, dplus, P.beta);
-      qL[j][k] = fma_(T(0.5), s, q[j][k]);
-      qR[j][k] = fma_(T(-0.5), s, q[j][k]);
+      const T h = limiter_half<T, LIM>(dminus, dplus, P.beta);
+      qL[j][k] = q[j][k] + h;
+      qR[j][k] = q[j][k] - h;
       dminus = dplus;
     }
   }
@@ -275,7 +278,7 @@ __device__ __forceinline__ void read_row(const T* buf, int lane, T V[CPL][4]) {
 // State of the y-march: three register slots indexed by row mod 3.
 template <typename T, int CPL> struct March {
   T q[3][CPL][4];  // primitives of rows r, r+1, r+2
-  T s[3][CPL][4];  // y-slopes
+  T s[3][CPL][4];  // half y-slopes (limiter_half)
   T G[3][CPL][4];  // G[slot(r)] = flux through face r-1/2
 };
 
@@ -291,26 +294,32 @@ template <typename T, int STAGE, int CPL> struct StageArgs {
 __device__ __forceinline__ int ring_slot(int row, int j0, int n) { return (row - j0 + 2 * n) % n; }
 
 // One row of the march.  S = slot of row r in the register window.
+// ring slot of row r + k, given si = slot of row r (0 <= k < RING_IN)
+__device__ __forceinline__ int ring_in_plus(int si, int k) {
+  const int t = si + k;
+  return t >= RING_IN ? t - RING_IN : t;
+}
+
 template <typename T, int LIM, int STAGE, int CPL, int S>
 __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, const StageArgs<T, STAGE, CPL>& A,
-                                          const LaneCols<CPL>& L, March<T, CPL>& M, int lane, int r, int jend,
-                                          T cx, T cy, T& smax, bool& bad) {
+                                          const LaneCols<CPL>& L, March<T, CPL>& M, int lane, int r, int si,
+                                          int jend, T cx, T cy, T& smax, bool& bad) {
   constexpr int S1 = (S + 1) % 3, S2 = (S + 2) % 3;
   constexpr int ROW = Ring<T, CPL>::ROW;
+  static_assert(RING_UN == 3, "the U^n ring is indexed by the register slot");
   // the group issued two rows ago (input row r+2, U^n row r) has landed
   cp_wait<1>();
   {
     T Ut[CPL][4];
-    read_row<T, CPL>(A.ring_in + ring_slot(r + 2, A.j0, RING_IN) * ROW, lane, Ut);
+    read_row<T, CPL>(A.ring_in + ring_in_plus(si, 2) * ROW, lane, Ut);
 #pragma unroll
     for (int j = 0; j < CPL; ++j) to_prim(P, Ut[j], M.q[S2][j]);
   }
   if (r + 2 < jend) {
-    issue_row<T, CPL>(A.ring_in + ring_slot(r + AHEAD_IN, A.j0, RING_IN) * ROW, A.P, L,
+    issue_row<T, CPL>(A.ring_in + ring_in_plus(si, AHEAD_IN) * ROW, A.P, L,
                       map_row(r + AHEAD_IN, m.ny, m.bc) * m.pitch, lane);
-    if (STAGE == 1 && L.any_out)
-      issue_out_cells<T, CPL>(A.ring_un + ring_slot(r + AHEAD_UN, A.j0, RING_UN) * ROW, A.N, L,
-                              (r + AHEAD_UN) * m.pitch, lane);
+    if (STAGE == 1 && L.any_out)  // U^n row r+2 lives in register slot S2's ring buffer
+      issue_out_cells<T, CPL>(A.ring_un + S2 * ROW, A.N, L, (r + AHEAD_UN) * m.pitch, lane);
   }
   cp_commit();
   // y-slopes of row r+1 and the flux through face r+1/2
@@ -319,9 +328,9 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, c
     T Lq[4], Rq[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      M.s[S1][j][k] = limiter<T, LIM>(M.q[S1][j][k] - M.q[S][j][k], M.q[S2][j][k] - M.q[S1][j][k], P.beta);
-      Lq[k] = fma_(T(0.5), M.s[S][j][k], M.q[S][j][k]);
-      Rq[k] = fma_(T(-0.5), M.s[S1][j][k], M.q[S1][j][k]);
+      M.s[S1][j][k] = limiter_half<T, LIM>(M.q[S1][j][k] - M.q[S][j][k], M.q[S2][j][k] - M.q[S1][j][k], P.beta);
+      Lq[k] = M.q[S][j][k] + M.s[S][j][k];
+      Rq[k] = M.q[S1][j][k] - M.s[S1][j][k];
     }
     lagrange_flux<T, 1>(P, Lq, Rq, M.G[S1][j]);
   }
@@ -331,8 +340,8 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, c
   if (!L.any_out) return;
   // update the output cells of row r
   T U[CPL][4], Un[CPL][4];
-  read_row<T, CPL>(A.ring_in + ring_slot(r, A.j0, RING_IN) * ROW, lane, U);
-  if (STAGE == 1) read_row<T, CPL>(A.ring_un + ring_slot(r, A.j0, RING_UN) * ROW, lane, Un);
+  read_row<T, CPL>(A.ring_in + si * ROW, lane, U);
+  if (STAGE == 1) read_row<T, CPL>(A.ring_un + S * ROW, lane, Un);
   T W[CPL][4];
 #pragma unroll
   for (int j = 0; j < CPL; ++j)
@@ -400,8 +409,7 @@ __device__ __forceinline__ void strip_tile(const Phys<T>& P, const MeshDesc& m, 
   cp_commit();
   issue_row<T, CPL>(A.ring_in + ring_slot(j0 + 2, j0, RING_IN) * ROW, A.P, L, map_row(j0 + 2, m.ny, m.bc) * m.pitch,
                     lane);
-  if (STAGE == 1 && L.any_out)
-    issue_out_cells<T, CPL>(A.ring_un + ring_slot(j0, j0, RING_UN) * ROW, A.N, L, j0 * m.pitch, lane);
+  if (STAGE == 1 && L.any_out) issue_out_cells<T, CPL>(A.ring_un + 0 * ROW, A.N, L, j0 * m.pitch, lane);
   cp_commit();
   cp_wait<1>();
   March<T, CPL> M;
@@ -420,10 +428,10 @@ __device__ __forceinline__ void strip_tile(const Phys<T>& P, const MeshDesc& m, 
       T Lq[4], Rq[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        M.s[2][j][k] = limiter<T, LIM>(M.q[2][j][k] - qm2[j][k], M.q[0][j][k] - M.q[2][j][k], P.beta);
-        M.s[0][j][k] = limiter<T, LIM>(M.q[0][j][k] - M.q[2][j][k], M.q[1][j][k] - M.q[0][j][k], P.beta);
-        Lq[k] = fma_(T(0.5), M.s[2][j][k], M.q[2][j][k]);
-        Rq[k] = fma_(T(-0.5), M.s[0][j][k], M.q[0][j][k]);
+        M.s[2][j][k] = limiter_half<T, LIM>(M.q[2][j][k] - qm2[j][k], M.q[0][j][k] - M.q[2][j][k], P.beta);
+        M.s[0][j][k] = limiter_half<T, LIM>(M.q[0][j][k] - M.q[2][j][k], M.q[1][j][k] - M.q[0][j][k], P.beta);
+        Lq[k] = M.q[2][j][k] + M.s[2][j][k];
+        Rq[k] = M.q[0][j][k] - M.s[0][j][k];
       }
       lagrange_flux<T, 1>(P, Lq, Rq, M.G[0][j]);
     }
@@ -432,25 +440,36 @@ __device__ __forceinline__ void strip_tile(const Phys<T>& P, const MeshDesc& m, 
     issue_row<T, CPL>(A.ring_in + ring_slot(j0 + 3, j0, RING_IN) * ROW, A.P, L,
                       map_row(j0 + 3, m.ny, m.bc) * m.pitch, lane);
     if (STAGE == 1 && L.any_out)
-      issue_out_cells<T, CPL>(A.ring_un + ring_slot(j0 + 1, j0, RING_UN) * ROW, A.N, L, (j0 + 1) * m.pitch, lane);
+      issue_out_cells<T, CPL>(A.ring_un + 1 * ROW, A.N, L, (j0 + 1) * m.pitch, lane);
   }
   cp_commit();
 
-  for (int r = j0;;) {
-    march_row<T, LIM, STAGE, CPL, 0>(P, m, A, L, M, lane, r, jend, cx, cy, smax, bad);
+  // si: input-ring slot of row r (row j0 is in slot 0)
+  for (int r = j0, si = 0;;) {
+    march_row<T, LIM, STAGE, CPL, 0>(P, m, A, L, M, lane, r, si, jend, cx, cy, smax, bad);
     if (++r >= jend) break;
-    march_row<T, LIM, STAGE, CPL, 1>(P, m, A, L, M, lane, r, jend, cx, cy, smax, bad);
+    si = ring_in_plus(si, 1);
+    march_row<T, LIM, STAGE, CPL, 1>(P, m, A, L, M, lane, r, si, jend, cx, cy, smax, bad);
     if (++r >= jend) break;
-    march_row<T, LIM, STAGE, CPL, 2>(P, m, A, L, M, lane, r, jend, cx, cy, smax, bad);
+    si = ring_in_plus(si, 1);
+    march_row<T, LIM, STAGE, CPL, 2>(P, m, A, L, M, lane, r, si, jend, cx, cy, smax, bad);
     if (++r >= jend) break;
+    si = ring_in_plus(si, 1);
   }
   cp_wait_all();
 }
 
 // One mesh: a 2D grid of (strips / STAGE_WARPS) x (row tiles) CTAs.
 // Dynamic shared memory: STAGE_WARPS * Ring<T,CPL>::warp_bytes(STAGE).
+// Resident CTAs per SM requested from the register allocator: FP32 stages are
+// issue-bound and gain from more warps (predictor 18 CTAs -> 92 registers,
+// corrector 16 -> 114, no spills); FP64 is bound by its arithmetic pipe and
+// keeps the registers it wants.
+template <typename T, int STAGE> struct MinBlocks { static constexpr int value = STAGE == 0 ? LF_MIN_BLOCKS0 : LF_MIN_BLOCKS1; };
+template <int STAGE> struct MinBlocks<double, STAGE> { static constexpr int value = 1; };
+
 template <typename T, int LIM, int STAGE, int CPL, int TY>
-__global__ void __launch_bounds__(STAGE_WARPS * 32, LF_MIN_BLOCKS)
+__global__ void __launch_bounds__(STAGE_WARPS * 32, (MinBlocks<T, STAGE>::value))
 stage2d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out, Scalars* sc) {
   extern __shared__ __align__(16) unsigned char lf_stage_smem[];
   const double dtd = sc->dt;
@@ -475,10 +494,13 @@ stage2d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
 // row tile) from an atomic counter until the list is exhausted.  Each problem
 // uses its own dt, and its corrector units feed its own wave-speed maximum.
 #ifndef LF_BATCH_MIN_BLOCKS
-#define LF_BATCH_MIN_BLOCKS 4
+#define LF_BATCH_MIN_BLOCKS (16 / LF_STAGE_WARPS)
 #endif
+template <typename T> struct BatchMinBlocks { static constexpr int value = LF_BATCH_MIN_BLOCKS; };
+template <> struct BatchMinBlocks<double> { static constexpr int value = 1; };
+
 template <typename T, int LIM, int STAGE, int CPL>
-__global__ void __launch_bounds__(STAGE_WARPS * 32, LF_BATCH_MIN_BLOCKS)
+__global__ void __launch_bounds__(STAGE_WARPS * 32, (BatchMinBlocks<T>::value))
 batch_stage_kernel(const BatchDesc b, const T* Uin, const T* Un, T* out, Scalars* sc, int* counter) {
   extern __shared__ __align__(16) unsigned char lf_stage_smem[];
   constexpr unsigned FULL = 0xffffffffu;
