@@ -315,12 +315,15 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, c
 #pragma unroll
     for (int j = 0; j < CPL; ++j) to_prim(P, Ut[j], M.q[S2][j]);
   }
-  if (r + 2 < jend) {
-    issue_row<T, CPL>(A.ring_in + ring_in_plus(si, AHEAD_IN) * ROW, A.P, L,
-                      map_row(r + AHEAD_IN, m.ny, m.bc) * m.pitch, lane);
-    if (STAGE == 1 && L.any_out)  // U^n row r+2 lives in register slot S2's ring buffer
-      issue_out_cells<T, CPL>(A.ring_un + S2 * ROW, A.N, L, (r + AHEAD_UN) * m.pitch, lane);
-  }
+  // Rows r+4 (input) and r+2 (U^n) are issued on every row, also near the
+  // end of the tile where they are not needed: the row index stays valid
+  // (boundary-mapped, or clamped to the last row) and the target buffers
+  // (rows r-1) are no longer read, so the branch-free row body costs two idle
+  // copies per tile.  strip_tile drains them before returning.
+  issue_row<T, CPL>(A.ring_in + ring_in_plus(si, AHEAD_IN) * ROW, A.P, L, map_row(r + AHEAD_IN, m.ny, m.bc) * m.pitch,
+                    lane);
+  if (STAGE == 1 && L.any_out)  // U^n row r+2 lives in register slot S2's ring buffer
+    issue_out_cells<T, CPL>(A.ring_un + S2 * ROW, A.N, L, min(r + AHEAD_UN, m.ny - 1) * m.pitch, lane);
   cp_commit();
   // y-slopes of row r+1 and the flux through face r+1/2
 #pragma unroll
@@ -337,8 +340,8 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, c
   // x-faces of row r
   T Fl[CPL][4], Fr[CPL][4];
   x_fluxes<T, LIM, CPL>(P, M.q[S], Fl, Fr);
-  if (!L.any_out) return;
-  // update the output cells of row r
+  // update the output cells of row r (computed on every lane; only output
+  // cells are stored and enter the wave-speed maximum)
   T U[CPL][4], Un[CPL][4];
   read_row<T, CPL>(A.ring_in + si * ROW, lane, U);
   if (STAGE == 1) read_row<T, CPL>(A.ring_un + S * ROW, lane, Un);
@@ -351,7 +354,7 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, c
       W[j][k] = fma_(-cy, M.G[S1][j][k] - M.G[S][j][k], fma_(-cx, Fr[j][k] - Fl[j][k], base));
     }
   const int off = r * m.pitch;
-  if (L.vec_ok) {
+  if (L.vec_ok && L.any_out) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       T v[CPL];
@@ -359,7 +362,7 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, c
       for (int j = 0; j < CPL; ++j) v[j] = W[j][k];
       VecLoad<T, CPL>::store(A.O[k] + off + L.c0, v);
     }
-  } else {
+  } else if (!L.vec_ok) {
 #pragma unroll
     for (int j = 0; j < CPL; ++j)
       if (L.out[j])
@@ -368,12 +371,12 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, c
   }
   if (STAGE == 1) {
 #pragma unroll
-    for (int j = 0; j < CPL; ++j)
-      if (L.out[j]) {
-        bool ok;
-        smax = fmax(smax, cell_speed<T, 2>(P, W[j], ok));
-        bad |= !ok;
-      }
+    for (int j = 0; j < CPL; ++j) {
+      bool ok;
+      const T sp = cell_speed<T, 2>(P, W[j], ok);
+      smax = L.out[j] ? fmax(smax, sp) : smax;
+      bad |= L.out[j] && !ok;
+    }
   }
 }
 
