@@ -180,6 +180,22 @@ def measured_traffic(kernel: str, cells: int):
         return None
 
 
+def fp64_alu_roofline(stage_ms, cells):
+    """FP64 ALU roofline of the FP64 corrector: executed FP64 flops per cell
+    (ncu counts of the committed capture, valid for the current kernel
+    sources) x cells / live kernel time, against the FP64 FMA peak."""
+    path = os.path.join(ROOT, "profiles", "fp64_flops.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    k = "stage2d_kernel<double, VANLEER, corrector>"
+    achieved = d["kernels"][k]["fp64_flops_per_cell"] * cells / (stage_ms[1] / 1e3) / 1e12
+    return {"bound": "alu", "kernel": k, "achieved": achieved, "peak": d["peak_tflops"], "unit": "TFLOP/s",
+            "frac": achieved / d["peak_tflops"], "peak_kind": "derived: " + d["peak_derivation"]}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -382,7 +398,7 @@ def run_ours(args, dist):
         del ref, got
         v64 = cells * args.fp64_steps / t64
         out["fp64"] = {"value": v64, "unit": METRIC, "steps": args.fp64_steps, "ms_per_step": 1e3 * t64 / args.fp64_steps,
-                       "stage_ms": [m0, m1]}
+                       "stage_ms": [m0, m1], "roofline": fp64_alu_roofline([m0, m1], cells)}
         out["fp32_over_fp64"] = value / dist.world / v64
         out["l1_error"] = {"fp32_vs_fp64_relative_l1": dict(zip(["rho", "rhou", "rhov", "rhoE"], l1)),
                            "after_steps": args.fp64_steps}

@@ -123,7 +123,9 @@ lf_status lf_step_fixed(lf_ctx* ctx, double dt);
 
 /* Advances until t reaches t_end (t_end <= 0: no final time) or max_steps
  * steps are done.  The last dt is clipped so that t lands on t_end.  dt stays
- * on the device; the host only polls t between batches of steps.
+ * on the device; steps are issued in batches of 32, each one replay of a
+ * CUDA graph recorded on first use (direct launches while stage tracing is
+ * on), and the host polls t only between batches.
  * steps_done and t_out are nullable; the call synchronises. */
 lf_status lf_run(lf_ctx* ctx, double t_end, int32_t max_steps, int32_t* steps_done, double* t_out);
 

@@ -203,6 +203,8 @@ void lf_destroy(lf_ctx* c) {
     cudaFree(c->dsums);
     cudaFreeHost(c->hsc);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->run_graph) cudaGraphExecDestroy(c->run_graph);
+    if (c->capture) cudaStreamDestroy(c->capture);
     lf::free_adjoint(c);
   }
   delete c;
@@ -398,6 +400,44 @@ lf_status lf_step_fixed(lf_ctx* c, double dt) {
   return enqueue_step(c, dt);
 }
 
+namespace {
+
+constexpr int kRunBatch = 32;  // steps per graph replay in lf_run
+
+// kRunBatch steps as one graph launch (steps past t_end are device-side
+// no-ops).  Falls back to direct launches while stage tracing is on, since
+// the tracing events are host-side bookkeeping.
+lf_status enqueue_batch(lf_ctx* c, int nsteps) {
+  if (nsteps != kRunBatch || c->profiling) {
+    for (int k = 0; k < nsteps; ++k)
+      if (lf_status st = enqueue_step(c, 0.0)) return st;
+    return LF_OK;
+  }
+  if (!c->run_graph) {
+    if (!c->capture) LF_CUDA(c, cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking));
+    LF_CUDA(c, cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeRelaxed));
+    cudaStream_t user = c->stream;
+    c->stream = c->capture;
+    lf_status st = LF_OK;
+    for (int k = 0; k < nsteps && st == LF_OK; ++k) st = enqueue_step(c, 0.0);
+    c->stream = user;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->capture, &graph);
+    if (st != LF_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->run_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+  }
+  LF_CUDA(c, cudaGraphLaunch(c->run_graph, c->stream));
+  return LF_OK;
+}
+
+}  // namespace
+
 lf_status lf_run(lf_ctx* c, double t_end, int32_t max_steps, int32_t* steps_done, double* t_out) {
   if (!c) return LF_ERR_ARG;
   if (max_steps < 0 || !std::isfinite(t_end)) {
@@ -412,15 +452,14 @@ lf_status lf_run(lf_ctx* c, double t_end, int32_t max_steps, int32_t* steps_done
   if (lf_status st = read_scalars(c)) return st;
   const long long steps0 = c->hsc->steps;
   LF_CUDA(c, lf::launch_set_t_end(c->sc, t_end > 0.0 ? t_end : 0.0, c->stream));
-  // Steps are enqueued in batches; with a final time the host polls t
-  // between batches, and steps past t_end are device-side no-ops.
-  const int batch = t_end > 0.0 ? 32 : max_steps;
+  // Steps are enqueued in batches of kRunBatch (one graph replay each); with
+  // a final time the host polls t between batches, and steps past t_end are
+  // device-side no-ops.
   int launched = 0;
   lf_status st = LF_OK;
   while (launched < max_steps) {
-    const int nb = max_steps - launched < batch ? max_steps - launched : batch;
-    for (int k = 0; k < nb && st == LF_OK; ++k) st = enqueue_step(c, 0.0);
-    if (st != LF_OK) break;
+    const int nb = max_steps - launched < kRunBatch ? max_steps - launched : kRunBatch;
+    if ((st = enqueue_batch(c, nb)) != LF_OK) break;
     launched += nb;
     if (t_end > 0.0 || launched >= max_steps) {
       if ((st = read_scalars(c)) != LF_OK) break;

@@ -22,6 +22,10 @@ struct lf_ctx {
   double* partials = nullptr; // conservation-sum partials
   double* dsums = nullptr;    // 4 device doubles
   bool has_state = false;
+  // lf_run replays a CUDA graph of kRunBatch steps (recorded once, on a
+  // private stream; replayed on `stream`)
+  cudaStream_t capture = nullptr;
+  cudaGraphExec_t run_graph = nullptr;
   // stage tracing: event pairs recorded around each stage launch
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;

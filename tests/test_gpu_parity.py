@@ -268,3 +268,26 @@ def test_full_size_8192_sampled_cells(precision):
         scale = np.abs(ref).max()
         assert np.abs(got - ref).max() <= tol * scale, (ci, cj, got, ref)
     s.close()
+
+
+def test_run_graph_replay_equals_direct_steps():
+    # lf_run issues steps as replays of a recorded 32-step CUDA graph plus a
+    # direct remainder; lf_step launches directly.  Same kernels, same order:
+    # the results must be identical bit for bit.
+    prim = inputs.kelvin_helmholtz(96, 80, seed=3).stack()
+    cfg = Config(nx=96, ny=80, bc="periodic", limiter="vanleer", cfl=0.45, precision="fp32")
+    outs = []
+    for mode in ("run", "step"):
+        s = LagrangeFlux(cfg)
+        q = torch.from_numpy(prim).cuda().float()
+        s.set_primitive(q[0], q[1], q[2], q[3])
+        if mode == "run":
+            n, _ = s.run(max_steps=70)
+            assert n == 70
+        else:
+            for _ in range(70):
+                s.step()
+        outs.append((s.get_state(), s.time()))
+        s.close()
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
