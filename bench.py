@@ -157,10 +157,14 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # helpers
 # ---------------------------------------------------------------------------
+KERNEL_SOURCES = ("lf_device.cuh", "lf_stage.cuh", "lf_internal.h", "lf_kernels_f32.cu", "lf_kernels_f64.cu")
+
+
 def kernel_source_hash() -> str:
+    """Hash of the device code that the stage kernels are compiled from."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1607_08710_gb300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1607_08710_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
