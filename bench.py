@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-rk3", action="store_true")
+    ap.add_argument("--rk3-steps", type=int, default=100)
     ap.add_argument("--batch-problems", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=300)
     return ap.parse_args()
@@ -406,6 +408,33 @@ def run_ours(args, dist):
         out["fp32_over_fp64"] = value / dist.world / v64
         out["l1_error"] = {"fp32_vs_fp64_relative_l1": dict(zip(["rho", "rhou", "rhov", "rhoE"], l1)),
                            "after_steps": args.fp64_steps}
+        torch.cuda.empty_cache()
+
+    # the same workload with the third-order SSP Runge-Kutta integrator (three fused stages per step)
+    if not args.no_rk3 and dist.rank == 0:
+        s3 = LagrangeFlux(Config(precision=prec, time_order=3, **kw))
+        q = torch.from_numpy(prim).to(dev, tdt)
+        s3.set_primitive(q[0], q[1], q[2], q[3])
+        del q
+        for _ in range(args.warmup):
+            s3.step()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.rk3_steps):
+            s3.step()
+        e1.record()
+        torch.cuda.synchronize()
+        t3 = e0.elapsed_time(e1) / 1e3
+        s3.sync()
+        s3.profile(True)
+        for _ in range(5):
+            s3.step()
+        (a0, a1), (c0, c1) = s3.profile_read()
+        s3.close()
+        out["rk3"] = {"value": cells * args.rk3_steps / t3, "unit": METRIC, "steps": args.rk3_steps,
+                      "ms_per_step": 1e3 * t3 / args.rk3_steps, "first_stage_ms": a0 / c0,
+                      "later_stage_ms": a1 / c1, "integrator": "SSP-RK3 (Shu-Osher), 3 fused stages per step"}
         torch.cuda.empty_cache()
 
     # batched: 512 seeded uneven meshes, one persistent launch per stage, graph of the step loop

@@ -68,6 +68,12 @@ enum { LF_FP64 = 0, LF_FP32 = 1 };
 /* Interface solver: eqs. (13)-(14) with a = max(c_L, c_R) (default), or the
  * acoustic solver with per-side impedances Z_k = rho_k c_k. */
 enum { LF_RIEMANN_MAXC = 0, LF_RIEMANN_PER_SIDE = 1 };
+/* Time integrator (Sec. 4: "RK2, etc."): the Heun scheme of Sec. 4 (0 or 2),
+ * or the third-order strong-stability-preserving Runge-Kutta scheme of Shu
+ * and Osher (3), U1 = U + dt L(U), U2 = 3/4 U + 1/4 (U1 + dt L(U1)),
+ * U' = 1/3 U + 2/3 (U2 + dt L(U2)).  SSP-RK3 needs one more state buffer and
+ * is offered by lf_init contexts only. */
+enum { LF_TIME_HEUN = 2, LF_TIME_SSPRK3 = 3 };
 
 typedef struct lf_config {
   int32_t dim;       /* 1 or 2 */
@@ -77,6 +83,8 @@ typedef struct lf_config {
   int32_t precision; /* LF_FP64 or LF_FP32 */
   int32_t riemann;   /* LF_RIEMANN_* */
   int32_t device;    /* CUDA device ordinal */
+  int32_t time_order; /* LF_TIME_* (0 = LF_TIME_HEUN) */
+  int32_t reserved;  /* must be 0 */
   double xmin, xmax; /* domain in x */
   double ymin, ymax; /* domain in y (ignored in 1D) */
   double gamma;      /* ratio of specific heats, 1 < gamma <= 3 (Sec. 3) */

@@ -90,6 +90,8 @@ struct OracleConfig {
   double gamma;     // perfect-gas ratio of specific heats, in (1, 3]
   double cfl;       // CFL number
   double beta;      // Sweby coefficient, in [1, 2]
+  int32_t time_order;  // 2: Heun (Sec. 4); 3: third-order SSP Runge-Kutta
+  int32_t pad;
 };
 
 bool config_ok(const OracleConfig* c) {
@@ -102,6 +104,7 @@ bool config_ok(const OracleConfig* c) {
   if (c->riemann < 0 || c->riemann > 1) return false;
   if (!(c->dx > 0) || (c->dim == 2 && !(c->dy > 0))) return false;
   if (!(c->gamma > 1.0)) return false;
+  if (c->time_order != 2 && c->time_order != 3) return false;
   return true;
 }
 
@@ -359,6 +362,52 @@ bool heun_step(const OracleConfig& c, std::vector<S> U[4], double dt) {
   return ok;
 }
 
+// Third-order strong-stability-preserving Runge-Kutta step of Shu and Osher
+// (J. Comput. Phys. 77, 1988) for the semi-discrete scheme dU/dt = L(U),
+// L(U) = -(1/|K|) sum_A |A| Phi_A (Sec. 4 names "RK2, etc." as time advance
+// schemes):
+//   U1 = U^n + dt L(U^n)
+//   U2 = 3/4 U^n + 1/4 (U1 + dt L(U1))
+//   U^{n+1} = 1/3 U^n + 2/3 (U2 + dt L(U2))
+template <class S>
+bool ssprk3_step(const OracleConfig& c, std::vector<S> U[4], double dt) {
+  Mesh<S> m(c);
+  std::vector<S> Fx[4], Fy[4], U1[4], U2[4];
+  bool ok = all_face_fluxes(m, U, Fx, Fy);
+  for (int l = 0; l < 4; ++l) U1[l].resize(m.ncell());
+  for (int j = 0; j < m.ny; ++j)
+    for (int i = 0; i < m.nx; ++i) {
+      size_t k = (size_t)j * m.nx + i;
+      for (int l = 0; l < 4; ++l) U1[l][k] = U[l][k] - dt * flux_balance(m, Fx[l], Fy[l], i, j);
+    }
+  ok = all_face_fluxes(m, U1, Fx, Fy) && ok;
+  for (int l = 0; l < 4; ++l) U2[l].resize(m.ncell());
+  for (int j = 0; j < m.ny; ++j)
+    for (int i = 0; i < m.nx; ++i) {
+      size_t k = (size_t)j * m.nx + i;
+      for (int l = 0; l < 4; ++l)
+        U2[l][k] = 0.75 * U[l][k] + 0.25 * (U1[l][k] - dt * flux_balance(m, Fx[l], Fy[l], i, j));
+    }
+  ok = all_face_fluxes(m, U2, Fx, Fy) && ok;
+  for (int j = 0; j < m.ny; ++j)
+    for (int i = 0; i < m.nx; ++i) {
+      size_t k = (size_t)j * m.nx + i;
+      for (int l = 0; l < 4; ++l)
+        U[l][k] = U[l][k] / 3.0 + (2.0 / 3.0) * (U2[l][k] - dt * flux_balance(m, Fx[l], Fy[l], i, j));
+    }
+  for (size_t k = 0; k < m.ncell(); ++k) {
+    S Uc[4] = {U[0][k], U[1][k], U[2][k], U[3][k]}, q[4];
+    prim_from_cons(c, Uc, q);
+    if (!(val(q[0]) > 0.0) || !(val(q[3]) > 0.0)) ok = false;
+  }
+  return ok;
+}
+
+template <class S>
+bool time_step(const OracleConfig& c, std::vector<S> U[4], double dt) {
+  return c.time_order == 3 ? ssprk3_step(c, U, dt) : heun_step(c, U, dt);
+}
+
 void load_planes(const OracleConfig& c, const double* src, std::vector<double> U[4]) {
   size_t n = (size_t)c.nx * c.ny;
   for (int l = 0; l < 4; ++l) U[l].assign(src + l * n, src + (l + 1) * n);
@@ -448,7 +497,7 @@ int oracle_residual(const OracleConfig* c, const double* Uin, double* LU) {
   return ok ? ORC_OK : ORC_NONPHYSICAL;
 }
 
-// Runs up to max_steps Heun steps.  If dts_in is given, step n uses dts_in[n]
+// Runs up to max_steps time steps (Heun, or SSP-RK3 when time_order == 3).  If dts_in is given, step n uses dts_in[n]
 // (a frozen dt sequence); otherwise dt comes from the CFL condition and is
 // clipped so that t never passes t_end (t_end <= 0: no final time).  The run
 // stops early once t reaches t_end.  dts_out (nullable) receives the dt used
@@ -466,7 +515,7 @@ int oracle_run(const OracleConfig* c, double* Uio, int32_t max_steps, double t0,
     double dt = dts_in ? dts_in[n] : cfl_dt(*c, U);
     if (!dts_in && t_end > 0.0 && t + dt > t_end) dt = t_end - t;
     if (dts_out) dts_out[n] = dt;
-    if (!heun_step(*c, U, dt)) {
+    if (!time_step(*c, U, dt)) {
       status = ORC_NONPHYSICAL;
       ++n;
       t += dt;
@@ -498,7 +547,7 @@ int oracle_run_tangent(const OracleConfig* c, const double* q0, const double* dq
   }
   int status = ORC_OK;
   for (int s = 0; s < nsteps; ++s)
-    if (!heun_step(*c, U, dts[s])) status = ORC_NONPHYSICAL;
+    if (!time_step(*c, U, dts[s])) status = ORC_NONPHYSICAL;
   for (int l = 0; l < 4; ++l)
     for (size_t k = 0; k < n; ++k) {
       U_out[l * n + k] = U[l][k].v;

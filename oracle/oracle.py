@@ -51,6 +51,8 @@ class _Cfg(ctypes.Structure):
         ("gamma", ctypes.c_double),
         ("cfl", ctypes.c_double),
         ("beta", ctypes.c_double),
+        ("time_order", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
     ]
 
 
@@ -69,12 +71,14 @@ class OracleConfig:
     beta: float = 1.5
     lx: float = 1.0
     ly: float = 1.0
+    time_order: int = 2  # 2: Heun (Sec. 4), 3: third-order SSP Runge-Kutta
 
     def to_c(self) -> _Cfg:
         ny = self.ny if self.dim == 2 else 1
         return _Cfg(
             self.dim, self.nx, ny, LIMITERS[self.limiter], BCS[self.bc], RIEMANN[self.riemann],
             self.lx / self.nx, self.ly / ny if self.dim == 2 else 1.0, self.gamma, self.cfl, self.beta,
+            self.time_order, 0,
         )
 
 
@@ -253,7 +257,8 @@ class RunResult:
 
 def run(cfg: OracleConfig, U0, max_steps: int, t_end: float = 0.0, t0: float = 0.0,
         dts=None, allow_nonphysical: bool = False) -> RunResult:
-    """Heun/RK2 Lagrange-flux steps (Sec. 4).  dts freezes the dt sequence."""
+    """Lagrange-flux steps (Sec. 4): Heun/RK2, or SSP-RK3 if cfg.time_order == 3.
+    dts freezes the dt sequence."""
     U = _state(cfg, U0).copy()
     dts_in = None if dts is None else _f64(dts)
     if dts_in is not None and dts_in.size < max_steps:

@@ -52,6 +52,9 @@ const char* validate(const lf_config* c) {
   if (!(c->gamma > 1.0 && c->gamma <= 3.0)) return "gamma must be in (1, 3]";
   if (!(c->cfl > 0.0 && c->cfl <= 1.0)) return "cfl must be in (0, 1]";
   if (c->limiter == LF_LIMITER_SWEBY && !(c->beta >= 1.0 && c->beta <= 2.0)) return "beta must be in [1, 2]";
+  if (c->time_order != 0 && c->time_order != LF_TIME_HEUN && c->time_order != LF_TIME_SSPRK3)
+    return "time_order must be 0, 2 (Heun) or 3 (SSP-RK3)";
+  if (c->reserved != 0) return "reserved must be 0";
   return nullptr;
 }
 
@@ -74,16 +77,25 @@ lf_status trace_begin(lf_ctx* c, int stage, cudaEvent_t* stop) {
   return LF_OK;
 }
 
+// Stage `stage` of the step (see launch_stage): Heun 0 (U -> U*), 1 (U*, U -> U);
+// SSP-RK3 0 (U -> U1 in Ustar), 2 (U1, U -> U2), 3 (U2, U -> U).  Traced
+// launches are filed as the first stage (0) or a later stage (1).
 template <typename T>
 lf_status dispatch_stage(lf_ctx* c, int stage) {
   T* U = static_cast<T*>(c->U);
   T* Us = static_cast<T*>(c->Ustar);
+  T* U2 = static_cast<T*>(c->U2);
   cudaEvent_t stop = nullptr;
   if (c->profiling)
-    if (lf_status st = trace_begin(c, stage, &stop)) return st;
-  cudaError_t e = stage == 0 ? lf::launch_stage<T>(0, c->mesh, U, U, Us, c->sc, c->stream)
-                             : lf::launch_stage<T>(1, c->mesh, Us, U, U, c->sc, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, stage == 0 ? "predictor launch" : "corrector launch");
+    if (lf_status st = trace_begin(c, stage == 0 ? 0 : 1, &stop)) return st;
+  cudaError_t e;
+  switch (stage) {
+    case 0: e = lf::launch_stage<T>(0, c->mesh, U, U, Us, c->sc, c->stream); break;
+    case 1: e = lf::launch_stage<T>(1, c->mesh, Us, U, U, c->sc, c->stream); break;
+    case 2: e = lf::launch_stage<T>(2, c->mesh, Us, U, U2, c->sc, c->stream); break;
+    default: e = lf::launch_stage<T>(3, c->mesh, U2, U, U, c->sc, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "stage launch");
   if (stop) LF_CUDA(c, cudaEventRecord(stop, c->stream));
   return LF_OK;
 }
@@ -93,8 +105,11 @@ lf_status dispatch_stage(lf_ctx* c, int stage) {
 // begin (dt) -> predictor -> corrector -> end (t, steps, parity)
 lf_status lf::enqueue_step(lf_ctx* c, double dt_fixed) {
   LF_CUDA(c, lf::launch_begin_step(c->sc, dt_fixed, c->stream));
-  for (int stage = 0; stage < 2; ++stage) {
-    lf_status st = c->elem == 8 ? dispatch_stage<double>(c, stage) : dispatch_stage<float>(c, stage);
+  static const int heun[] = {0, 1}, rk3[] = {0, 2, 3};
+  const bool third = c->cfg.time_order == LF_TIME_SSPRK3;
+  const int* stages = third ? rk3 : heun;
+  for (int k = 0; k < (third ? 3 : 2); ++k) {
+    lf_status st = c->elem == 8 ? dispatch_stage<double>(c, stages[k]) : dispatch_stage<float>(c, stages[k]);
     if (st != LF_OK) return st;
   }
   LF_CUDA(c, lf::launch_end_step(c->sc, c->stream));
@@ -197,6 +212,7 @@ void lf_destroy(lf_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     cudaFree(c->U);
     cudaFree(c->Ustar);
+    cudaFree(c->U2);
     cudaFree(c->staging);
     cudaFree(c->sc);
     cudaFree(c->partials);
@@ -256,6 +272,7 @@ lf_status lf_init(const lf_config* cfg, void* stream, lf_ctx** out) {
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc(&c->U, state_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&c->Ustar, state_bytes);
+  if (e == cudaSuccess && cfg->time_order == LF_TIME_SSPRK3) e = cudaMalloc(&c->U2, state_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&c->sc, sizeof(lf::Scalars));
   if (e == cudaSuccess) e = cudaMalloc(&c->partials, (size_t)lf::sums_blocks() * 4 * 2 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->dsums, 4 * sizeof(double));

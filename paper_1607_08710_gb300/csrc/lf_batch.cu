@@ -90,6 +90,7 @@ const char* check_problem(const lf_config* c, const lf_config* c0) {
   if (!(c->gamma > 1.0 && c->gamma <= 3.0) || !(c->cfl > 0.0 && c->cfl <= 1.0)) return "gamma or cfl out of range";
   if (c->limiter == LF_LIMITER_SWEBY && !(c->beta >= 1.0 && c->beta <= 2.0)) return "beta out of range";
   if (c->device < 0) return "device must be >= 0";
+  if (c->time_order != 0 && c->time_order != LF_TIME_HEUN) return "batched mode runs the Heun time integrator";
   if (c0 && (c->limiter != c0->limiter || c->bc != c0->bc || c->precision != c0->precision ||
              c->riemann != c0->riemann || c->gamma != c0->gamma || c->cfl != c0->cfl || c->beta != c0->beta ||
              c->device != c0->device))

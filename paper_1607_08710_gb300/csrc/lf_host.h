@@ -15,7 +15,8 @@ struct lf_ctx {
   cudaStream_t stream = nullptr;
   size_t elem = 8;            // bytes per element
   void* U = nullptr;          // current state, 4 pitched planes
-  void* Ustar = nullptr;      // Heun predictor state, 4 pitched planes
+  void* Ustar = nullptr;      // Heun predictor / first RK3 stage, 4 pitched planes
+  void* U2 = nullptr;         // second SSP-RK3 stage (time_order 3 only)
   void* staging = nullptr;    // dense 4 planes for host primitive transfers (lazy)
   lf::Scalars* sc = nullptr;  // device scalars
   lf::Scalars* hsc = nullptr; // pinned host mirror for read-back

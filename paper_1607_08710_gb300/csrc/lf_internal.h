@@ -60,10 +60,13 @@ struct BatchDesc {
   int grid;               // persistent CTAs
 };
 
-// Per-stage launch of the fused stage kernel (one Heun stage over the mesh).
-// stage 0: out = Uin - dt L(Uin)                      (predictor, Heun step 6)
-// stage 1: out = (Un + Uin)/2 - dt/2 L(Uin)           (corrector, Heun step 11),
-//          also accumulates the new state's max wave speed for the next dt.
+// Per-stage launch of the fused stage kernel (one Runge-Kutta stage over the
+// mesh), out = alpha Un + beta (Uin - dt D(Uin)):
+// stage 0: alpha 0, beta 1       (Heun predictor, step 6; first SSP-RK3 stage)
+// stage 1: alpha 1/2, beta 1/2   (Heun corrector, step 11), also accumulates
+//          the new state's max wave speed for the next dt
+// stage 2: alpha 3/4, beta 1/4   (second SSP-RK3 stage)
+// stage 3: alpha 1/3, beta 2/3   (third SSP-RK3 stage, with the wave speed)
 // `out` may alias `Un` (stage 1 updates in place); Uin must not alias out.
 template <typename T>
 cudaError_t launch_stage(int stage, const MeshDesc& m, const T* Uin, const T* Un, T* out,

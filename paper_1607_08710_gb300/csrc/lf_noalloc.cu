@@ -72,6 +72,7 @@ const char* check_config(const lf_config* c) {
   if (!(c->xmax > c->xmin) || (c->dim == 2 && !(c->ymax > c->ymin))) return "empty domain";
   if (!(c->gamma > 1.0 && c->gamma <= 3.0) || !(c->cfl > 0.0 && c->cfl <= 1.0)) return "gamma or cfl out of range";
   if (c->limiter == LF_LIMITER_SWEBY && !(c->beta >= 1.0 && c->beta <= 2.0)) return "beta out of range";
+  if (c->time_order != 0 && c->time_order != LF_TIME_HEUN) return "only the Heun time integrator";
   return nullptr;
 }
 

@@ -275,6 +275,19 @@ __device__ __forceinline__ void read_row(const T* buf, int lane, T V[CPL][4]) {
   }
 }
 
+// Stages of the time integrators, out = alpha U^n + beta (Uin - dt D(Uin)):
+//   0: alpha 0,   beta 1    first stage of Heun (Sec. 4, step 6) and of SSP-RK3
+//   1: alpha 1/2, beta 1/2  Heun corrector (Sec. 4, step 11), + wave-speed max
+//   2: alpha 3/4, beta 1/4  second SSP-RK3 stage
+//   3: alpha 1/3, beta 2/3  third SSP-RK3 stage, + wave-speed max
+// Stages >= 1 read U^n at the cell; the last stage of a step feeds the CFL
+// maximum of the new state.
+template <int STAGE> struct StageCoef;
+template <> struct StageCoef<0> { static constexpr double alpha = 0.0, beta = 1.0; static constexpr bool speed = false; };
+template <> struct StageCoef<1> { static constexpr double alpha = 0.5, beta = 0.5; static constexpr bool speed = true; };
+template <> struct StageCoef<2> { static constexpr double alpha = 0.75, beta = 0.25; static constexpr bool speed = false; };
+template <> struct StageCoef<3> { static constexpr double alpha = 1.0 / 3.0, beta = 2.0 / 3.0; static constexpr bool speed = true; };
+
 // State of the y-march: three register slots indexed by row mod 3.
 template <typename T, int CPL> struct March {
   T q[3][CPL][4];  // primitives of rows r, r+1, r+2
@@ -322,7 +335,7 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, c
   // copies per tile.  strip_tile drains them before returning.
   issue_row<T, CPL>(A.ring_in + ring_in_plus(si, AHEAD_IN) * ROW, A.P, L, map_row(r + AHEAD_IN, m.ny, m.bc) * m.pitch,
                     lane);
-  if (STAGE == 1 && L.any_out)  // U^n row r+2 lives in register slot S2's ring buffer
+  if (STAGE >= 1 && L.any_out)  // U^n row r+2 lives in register slot S2's ring buffer
     issue_out_cells<T, CPL>(A.ring_un + S2 * ROW, A.N, L, min(r + AHEAD_UN, m.ny - 1) * m.pitch, lane);
   cp_commit();
   // y-slopes of row r+1 and the flux through face r+1/2
@@ -344,13 +357,15 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, c
   // cells are stored and enter the wave-speed maximum)
   T U[CPL][4], Un[CPL][4];
   read_row<T, CPL>(A.ring_in + si * ROW, lane, U);
-  if (STAGE == 1) read_row<T, CPL>(A.ring_un + S * ROW, lane, Un);
+  if (STAGE >= 1) read_row<T, CPL>(A.ring_un + S * ROW, lane, Un);
   T W[CPL][4];
 #pragma unroll
   for (int j = 0; j < CPL; ++j)
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const T base = STAGE == 0 ? U[j][k] : T(0.5) * (Un[j][k] + U[j][k]);
+      const T base = STAGE == 0 ? U[j][k]
+                    : STAGE == 1 ? T(0.5) * (Un[j][k] + U[j][k])
+                                 : fma_(T(StageCoef<STAGE>::alpha), Un[j][k], T(StageCoef<STAGE>::beta) * U[j][k]);
       W[j][k] = fma_(-cy, M.G[S1][j][k] - M.G[S][j][k], fma_(-cx, Fr[j][k] - Fl[j][k], base));
     }
   const int off = r * m.pitch;
@@ -369,7 +384,7 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, c
 #pragma unroll
         for (int k = 0; k < 4; ++k) A.O[k][off + L.c0 + j] = W[j][k];
   }
-  if (STAGE == 1) {
+  if (StageCoef<STAGE>::speed) {
 #pragma unroll
     for (int j = 0; j < CPL; ++j) {
       bool ok;
@@ -412,7 +427,7 @@ __device__ __forceinline__ void strip_tile(const Phys<T>& P, const MeshDesc& m, 
   cp_commit();
   issue_row<T, CPL>(A.ring_in + ring_slot(j0 + 2, j0, RING_IN) * ROW, A.P, L, map_row(j0 + 2, m.ny, m.bc) * m.pitch,
                     lane);
-  if (STAGE == 1 && L.any_out) issue_out_cells<T, CPL>(A.ring_un + 0 * ROW, A.N, L, j0 * m.pitch, lane);
+  if (STAGE >= 1 && L.any_out) issue_out_cells<T, CPL>(A.ring_un + 0 * ROW, A.N, L, j0 * m.pitch, lane);
   cp_commit();
   cp_wait<1>();
   March<T, CPL> M;
@@ -442,7 +457,7 @@ __device__ __forceinline__ void strip_tile(const Phys<T>& P, const MeshDesc& m, 
   if (j0 + 1 < jend) {
     issue_row<T, CPL>(A.ring_in + ring_slot(j0 + 3, j0, RING_IN) * ROW, A.P, L,
                       map_row(j0 + 3, m.ny, m.bc) * m.pitch, lane);
-    if (STAGE == 1 && L.any_out)
+    if (STAGE >= 1 && L.any_out)
       issue_out_cells<T, CPL>(A.ring_un + 1 * ROW, A.N, L, (j0 + 1) * m.pitch, lane);
   }
   cp_commit();
@@ -484,13 +499,13 @@ stage2d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
   if (i0 >= m.nx) return;  // whole warp
   const int j0 = blockIdx.y * TY;
   const int jend = min(j0 + TY, m.ny);
-  const double hs = STAGE == 0 ? 1.0 : 0.5;
+  const double hs = StageCoef<STAGE>::beta;
   const T cx = T(hs * dtd * m.rdx), cy = T(hs * dtd * m.rdy);
   T* ring = reinterpret_cast<T*>(lf_stage_smem + warp * Ring<T, CPL>::warp_bytes(STAGE));
   T smax = T(0);
   bool bad = false;
   strip_tile<T, LIM, STAGE, CPL>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring, lane, smax, bad);
-  if (STAGE == 1) publish_speed(sc, wpar, smax, bad);
+  if (StageCoef<STAGE>::speed) publish_speed(sc, wpar, smax, bad);
 }
 
 // Many meshes: a persistent grid whose warps pull work units (problem, strip,
@@ -527,13 +542,13 @@ batch_stage_kernel(const BatchDesc b, const T* Uin, const T* Un, T* out, Scalars
     m.rdx = pd.rdx;
     m.rdy = pd.rdy;
     const Phys<T> P(m);
-    const double hs = STAGE == 0 ? 1.0 : 0.5;
+    const double hs = StageCoef<STAGE>::beta;
     const T cx = T(hs * dtd * m.rdx), cy = T(hs * dtd * m.rdy);
     T smax = T(0);
     bool bad = false;
     strip_tile<T, LIM, STAGE, CPL>(P, m, Uin + pd.off, Un + pd.off, out + pd.off, un.i0, un.j0, un.jend, cx, cy,
                                    ring, lane, smax, bad);
-    if (STAGE == 1) publish_speed(scp, scp->parity ^ 1, smax, bad);
+    if (StageCoef<STAGE>::speed) publish_speed(scp, scp->parity ^ 1, smax, bad);
   }
 }
 
@@ -570,7 +585,7 @@ stage1d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
   const int i0 = (blockIdx.x * STAGE_WARPS + (threadIdx.x >> 5)) * StripGeom<CPL>::OUT;
   if (i0 >= m.nx) return;
   const LaneCols<CPL> L = lane_cols<CPL>(i0, lane, m.nx, m.bc, m.vec);
-  const T cx = T((STAGE == 0 ? 1.0 : 0.5) * dtd * m.rdx);
+  const T cx = T(StageCoef<STAGE>::beta * dtd * m.rdx);
   const T* Pp[4] = {Uin, Uin + m.plane, Uin + 2 * m.plane, Uin + 3 * m.plane};
   T U[CPL][4], q[CPL][4], Fl[CPL][4], Fr[CPL][4];
   load_row<T, CPL>(Pp, L, 0, U);
@@ -586,18 +601,20 @@ stage1d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
     T W[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const T base = STAGE == 0 ? U[j][k] : T(0.5) * (Un[k * m.plane + c] + U[j][k]);
+      const T base = STAGE == 0 ? U[j][k]
+                    : STAGE == 1 ? T(0.5) * (Un[k * m.plane + c] + U[j][k])
+                                 : fma_(T(StageCoef<STAGE>::alpha), Un[k * m.plane + c], T(StageCoef<STAGE>::beta) * U[j][k]);
       W[k] = fma_(-cx, Fr[j][k] - Fl[j][k], base);
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) out[k * m.plane + c] = W[k];
-    if (STAGE == 1) {
+    if (StageCoef<STAGE>::speed) {
       bool ok;
       smax = fmax(smax, cell_speed<T, 1>(P, W, ok));
       bad |= !ok;
     }
   }
-  if (STAGE == 1) publish_speed(sc, wpar, smax, bad);
+  if (StageCoef<STAGE>::speed) publish_speed(sc, wpar, smax, bad);
 }
 
 template <typename T, int LIM>
@@ -608,13 +625,21 @@ cudaError_t launch_stage_lim(int stage, const MeshDesc& m, const T* Uin, const T
   dim3 block(STAGE_WARPS * 32);
   if (m.dim == 1) {
     dim3 grid((strips + STAGE_WARPS - 1) / STAGE_WARPS);
-    if (stage == 0) stage1d_kernel<T, LIM, 0, CPL><<<grid, block, 0, s>>>(m, Uin, Un, out, sc);
-    else stage1d_kernel<T, LIM, 1, CPL><<<grid, block, 0, s>>>(m, Uin, Un, out, sc);
+    switch (stage) {
+      case 0: stage1d_kernel<T, LIM, 0, CPL><<<grid, block, 0, s>>>(m, Uin, Un, out, sc); break;
+      case 1: stage1d_kernel<T, LIM, 1, CPL><<<grid, block, 0, s>>>(m, Uin, Un, out, sc); break;
+      case 2: stage1d_kernel<T, LIM, 2, CPL><<<grid, block, 0, s>>>(m, Uin, Un, out, sc); break;
+      default: stage1d_kernel<T, LIM, 3, CPL><<<grid, block, 0, s>>>(m, Uin, Un, out, sc);
+    }
   } else {
     dim3 grid((strips + STAGE_WARPS - 1) / STAGE_WARPS, (m.ny + TY - 1) / TY);
     const size_t smem = STAGE_WARPS * Ring<T, CPL>::warp_bytes(stage);
-    if (stage == 0) stage2d_kernel<T, LIM, 0, CPL, TY><<<grid, block, smem, s>>>(m, Uin, Un, out, sc);
-    else stage2d_kernel<T, LIM, 1, CPL, TY><<<grid, block, smem, s>>>(m, Uin, Un, out, sc);
+    switch (stage) {
+      case 0: stage2d_kernel<T, LIM, 0, CPL, TY><<<grid, block, smem, s>>>(m, Uin, Un, out, sc); break;
+      case 1: stage2d_kernel<T, LIM, 1, CPL, TY><<<grid, block, smem, s>>>(m, Uin, Un, out, sc); break;
+      case 2: stage2d_kernel<T, LIM, 2, CPL, TY><<<grid, block, smem, s>>>(m, Uin, Un, out, sc); break;
+      default: stage2d_kernel<T, LIM, 3, CPL, TY><<<grid, block, smem, s>>>(m, Uin, Un, out, sc);
+    }
   }
   return cudaGetLastError();
 }

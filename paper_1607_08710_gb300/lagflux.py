@@ -34,6 +34,8 @@ class lf_config(ctypes.Structure):
         ("precision", ctypes.c_int32),
         ("riemann", ctypes.c_int32),
         ("device", ctypes.c_int32),
+        ("time_order", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
         ("xmin", ctypes.c_double),
         ("xmax", ctypes.c_double),
         ("ymin", ctypes.c_double),
@@ -118,11 +120,12 @@ class Config:
     ymin: float = 0.0
     ymax: float = 1.0
     device: int = 0
+    time_order: int = 2  # 2: Heun (Sec. 4), 3: SSP-RK3
 
     def to_c(self) -> lf_config:
         return lf_config(self.dim, self.nx, self.ny if self.dim == 2 else 1, LIMITERS[self.limiter], BCS[self.bc],
-                         PRECISIONS[self.precision], RIEMANN[self.riemann], self.device, self.xmin, self.xmax,
-                         self.ymin, self.ymax, self.gamma, self.cfl, self.beta)
+                         PRECISIONS[self.precision], RIEMANN[self.riemann], self.device, self.time_order, 0,
+                         self.xmin, self.xmax, self.ymin, self.ymax, self.gamma, self.cfl, self.beta)
 
     @property
     def np_dtype(self):

@@ -35,6 +35,7 @@ MUTANTS = {
     "max_c_is_min": ("S a = max_first(cL, cR);", "S a = min_first(cL, cR);"),
     "dt_without_y": ("if (c.dim == 2) s += (std::fabs(q[2]) + a) / c.dy;", ""),
     "momentum_pressure_wrong_axis": ("F[1 + dir] = F[1 + dir] + pstar;", "F[1] = F[1] + pstar;"),
+    "rk3_stage2_weight": ("U2[l][k] = 0.75 * U[l][k] + 0.25 *", "U2[l][k] = 0.70 * U[l][k] + 0.30 *"),
 }
 
 
@@ -109,6 +110,16 @@ def battery():
         except O.OracleError:
             errs.append(np.inf)
     check("order2", np.all(np.isfinite(errs)) and errs[1] > 0 and math.log2(errs[0] / errs[1]) > 1.8)
+    # SSP-RK3 step against its Butcher form built from the residual
+    c3 = O.OracleConfig(nx=10, ny=12, bc="periodic", time_order=3)
+    U3 = O.prim_to_cons(c3, inputs.kelvin_helmholtz(10, 12, seed=4).stack())
+    dt = 0.5 * O.cfl_dt(c3, U3)
+    k1 = O.residual(c3, U3)
+    k2 = O.residual(c3, U3 + dt * k1)
+    k3 = O.residual(c3, U3 + dt * (k1 + k2) / 4)
+    ref = U3 + dt * (k1 / 6 + k2 / 6 + 2 * k3 / 3)
+    got = O.run(c3, U3, 1, dts=[dt], allow_nonphysical=True).U
+    check("rk3_butcher", np.allclose(got, ref, rtol=1e-12, atol=1e-13))
     return fails
 
 

@@ -257,3 +257,38 @@ def test_tangent_matches_central_differences(state):
         fd = (Up - Um) / (2 * h)
         errs.append(np.abs(fd - dUT).max() / np.abs(dUT).max())
     assert min(errs) < 1e-6
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_time_steps_equal_butcher_form(order):
+    # The oracle's Heun (flux average) and SSP-RK3 (Shu-Osher convex
+    # combinations) steps against the same methods in Butcher form, built here
+    # from the oracle's residual L(U): Heun k1 = L(U), k2 = L(U + dt k1),
+    # U + dt (k1 + k2)/2; SSP-RK3 k3 = L(U + dt (k1 + k2)/4),
+    # U + dt (k1/6 + k2/6 + 2 k3/3).
+    n = 20
+    c = O.OracleConfig(nx=n, ny=n + 3, bc="periodic", limiter="vanleer", time_order=order)
+    U0 = O.prim_to_cons(c, inputs.kelvin_helmholtz(n, n + 3, seed=8).stack())
+    dt = 0.5 * O.cfl_dt(c, U0)
+    k1 = O.residual(c, U0)
+    k2 = O.residual(c, U0 + dt * k1)
+    if order == 2:
+        ref = U0 + dt * (k1 + k2) / 2
+    else:
+        k3 = O.residual(c, U0 + dt * (k1 + k2) / 4)
+        ref = U0 + dt * (k1 / 6 + k2 / 6 + 2 * k3 / 3)
+    got = O.run(c, U0, 1, dts=[dt]).U
+    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-14)
+
+
+def test_ssprk3_keeps_invariants():
+    n = 24
+    c = O.OracleConfig(nx=n, ny=n, bc="periodic", limiter="vanleer", time_order=3)
+    U0 = O.prim_to_cons(c, inputs.kelvin_helmholtz(n, n, seed=2).stack())
+    r = O.run(c, U0, 20)
+    s0, s1 = fsum_planes(U0), fsum_planes(r.U)
+    scale = np.array([math.fsum(np.abs(U0[l]).ravel()) for l in range(4)])
+    assert np.all(np.abs(s1 - s0) <= 1e-13 * scale)
+    cw = O.OracleConfig(nx=n, ny=n, bc="periodic", limiter="vanleer", time_order=3)
+    q = O.cons_to_prim(cw, O.run(cw, O.prim_to_cons(cw, inputs.smooth_wave(n).stack()), 20).U)
+    assert np.abs(q[1] - 0.5).max() < 1e-13 and np.abs(q[3] - 1.0).max() < 1e-13
