@@ -28,6 +28,13 @@
 //     L if u* > 0, else R.
 //   * Ghost cells: two layers; transmissive = copy of the boundary cell,
 //     periodic = wrap-around.
+//   * Species (Sec. 5, conservative form of the mass-fraction transport):
+//     each mass fraction y_k = (rho y_k)/rho is one more primitive variable,
+//     reconstructed with the same limiter as (rho, u, v, p); the edge value of
+//     rho y_k is rebuilt from the upwind primitive state like the other
+//     conservative variables, so its flux is (rho_A y_k,A) u*.  The species do
+//     not enter the pressure, the sound speed or the CFL condition (one gamma
+//     for the mixture).
 //   * Derivative conventions for the dual number at non-smooth points:
 //     max/min pick the first argument on ties, the limiter is 0 (with zero
 //     derivative) when ab <= 0, and the upwind branch follows the value of u*.
@@ -80,6 +87,9 @@ enum { BC_TRANSMISSIVE = 0, BC_PERIODIC = 1 };
 enum { RIEMANN_MAXC = 0, RIEMANN_PER_SIDE = 1 };
 enum { ORC_OK = 0, ORC_NONPHYSICAL = 1, ORC_ARG = 2 };
 
+constexpr int MAX_SPECIES = 8;
+constexpr int MAXF = 4 + MAX_SPECIES;  // largest number of transported fields
+
 struct OracleConfig {
   int32_t dim;      // 1 or 2
   int32_t nx, ny;   // cells (ny == 1 when dim == 1)
@@ -91,8 +101,11 @@ struct OracleConfig {
   double cfl;       // CFL number
   double beta;      // Sweby coefficient, in [1, 2]
   int32_t time_order;  // 2: Heun (Sec. 4); 3: third-order SSP Runge-Kutta
-  int32_t pad;
+  int32_t nspecies;    // transported mass fractions (Sec. 5), 0 .. MAX_SPECIES
 };
+
+// Fields per cell: (rho, rho u, rho v, rho E, rho y_1 .. rho y_nspecies).
+inline int nfields(const OracleConfig& c) { return 4 + c.nspecies; }
 
 bool config_ok(const OracleConfig* c) {
   if (!c) return false;
@@ -105,15 +118,17 @@ bool config_ok(const OracleConfig* c) {
   if (!(c->dx > 0) || (c->dim == 2 && !(c->dy > 0))) return false;
   if (!(c->gamma > 1.0)) return false;
   if (c->time_order != 2 && c->time_order != 3) return false;
+  if (c->nspecies < 0 || c->nspecies > MAX_SPECIES) return false;
   return true;
 }
 
 // ---------------------------------------------------------------------------
 // Eq. (1): perfect-gas EOS p = (gamma-1) rho (E - |u|^2/2), c = sqrt(gamma p / rho).
-// Primitive vector q = (rho, u, v, p); conservative U = (rho, rho u, rho v, rho E).
+// Primitive vector q = (rho, u, v, p, y_1 ..); conservative
+// U = (rho, rho u, rho v, rho E, rho y_1 ..), nfields(c) entries each.
 // ---------------------------------------------------------------------------
 template <class S>
-void prim_from_cons(const OracleConfig& c, const S U[4], S q[4]) {
+void prim_from_cons(const OracleConfig& c, const S U[], S q[]) {
   S rho = U[0];
   S u = U[1] / rho;
   S v = U[2] / rho;
@@ -122,15 +137,17 @@ void prim_from_cons(const OracleConfig& c, const S U[4], S q[4]) {
   q[1] = u;
   q[2] = v;
   q[3] = (c.gamma - 1.0) * rho * (E - 0.5 * (u * u + v * v));
+  for (int k = 0; k < c.nspecies; ++k) q[4 + k] = U[4 + k] / rho;
 }
 
 template <class S>
-void cons_from_prim(const OracleConfig& c, const S q[4], S U[4]) {
+void cons_from_prim(const OracleConfig& c, const S q[], S U[]) {
   S rho = q[0], u = q[1], v = q[2], p = q[3];
   U[0] = rho;
   U[1] = rho * u;
   U[2] = rho * v;
   U[3] = p / (c.gamma - 1.0) + 0.5 * rho * (u * u + v * v);
+  for (int k = 0; k < c.nspecies; ++k) U[4 + k] = rho * q[4 + k];
 }
 
 template <class S>
@@ -184,16 +201,17 @@ void interface_solve(const OracleConfig& c, const S& rL, const S& uL, const S& p
 // Eq. (12) with the upwinding of Sec. 4 (Heun steps 3-5): for a face with unit
 // normal nu along axis `dir` (0 = x, 1 = y), pointing from L to R,
 //   Phi = U_A (u* ) + (0, p* nu_x, p* nu_y, p* u*),
-// U_A = U(q_L) if u* > 0 else U(q_R).
+// U_A = U(q_L) if u* > 0 else U(q_R).  The species rows of Phi are
+// (rho y_k)_A u*, with no pressure term.
 // ---------------------------------------------------------------------------
 template <class S>
-void face_flux(const OracleConfig& c, int dir, const S qL[4], const S qR[4], S F[4]) {
+void face_flux(const OracleConfig& c, int dir, const S qL[], const S qR[], S F[]) {
   S pstar, ustar;
   interface_solve(c, qL[0], qL[1 + dir], qL[3], qR[0], qR[1 + dir], qR[3], pstar, ustar);
   const S* qup = (val(ustar) > 0.0) ? qL : qR;
-  S Uup[4];
+  S Uup[MAXF];
   cons_from_prim(c, qup, Uup);
-  for (int l = 0; l < 4; ++l) F[l] = Uup[l] * ustar;
+  for (int l = 0; l < nfields(c); ++l) F[l] = Uup[l] * ustar;
   F[1 + dir] = F[1 + dir] + pstar;
   F[3] = F[3] + pstar * ustar;
 }
@@ -228,9 +246,10 @@ struct Mesh {
 
 // Builds the ghost-extended primitive field from the conservative planes.
 template <class S>
-bool build_primitives(const Mesh<S>& m, const std::vector<S> U[4], std::vector<S> qg[4]) {
+bool build_primitives(const Mesh<S>& m, const std::vector<S> U[], std::vector<S> qg[]) {
   const OracleConfig& c = m.c;
-  for (int l = 0; l < 4; ++l) qg[l].assign((size_t)m.gx * m.gy, S(0.0));
+  const int nf = nfields(c);
+  for (int l = 0; l < nf; ++l) qg[l].assign((size_t)m.gx * m.gy, S(0.0));
   bool physical = true;
   int jlo = (c.dim == 2) ? -G : 0, jhi = (c.dim == 2) ? m.ny + G : 1;
   for (int j = jlo; j < jhi; ++j) {
@@ -239,12 +258,12 @@ bool build_primitives(const Mesh<S>& m, const std::vector<S> U[4], std::vector<S
       int si = wrap_index(i, m.nx, c.bc);
       int sj = (c.dim == 2) ? wrap_index(j, m.ny, c.bc) : 0;
       size_t s = (size_t)sj * m.nx + si;
-      S Uc[4] = {U[0][s], U[1][s], U[2][s], U[3][s]};
-      S q[4];
+      S Uc[MAXF], q[MAXF];
+      for (int l = 0; l < nf; ++l) Uc[l] = U[l][s];
       prim_from_cons(c, Uc, q);
       if (!(val(q[0]) > 0.0) || !(val(q[3]) > 0.0)) physical = false;
       size_t g = m.gidx(i, j);
-      for (int l = 0; l < 4; ++l) qg[l][g] = q[l];
+      for (int l = 0; l < nf; ++l) qg[l][g] = q[l];
     }
   }
   return physical;
@@ -254,46 +273,47 @@ bool build_primitives(const Mesh<S>& m, const std::vector<S> U[4], std::vector<S
 // Fx has (nx+1) x ny faces (face f of row j between cells f-1 and f),
 // Fy has nx x (ny+1) faces (face g of column i between cells g-1 and g).
 template <class S>
-bool all_face_fluxes(const Mesh<S>& m, const std::vector<S> U[4], std::vector<S> Fx[4],
-                     std::vector<S> Fy[4]) {
+bool all_face_fluxes(const Mesh<S>& m, const std::vector<S> U[], std::vector<S> Fx[],
+                     std::vector<S> Fy[]) {
   const OracleConfig& c = m.c;
-  std::vector<S> qg[4];
+  const int nf = nfields(c);
+  std::vector<S> qg[MAXF];
   bool physical = build_primitives(m, U, qg);
   auto q_at = [&](int l, int i, int j) -> S { return qg[l][m.gidx(i, j)]; };
 
   // x-faces
-  for (int l = 0; l < 4; ++l) Fx[l].assign((size_t)(m.nx + 1) * m.ny, S(0.0));
+  for (int l = 0; l < nf; ++l) Fx[l].assign((size_t)(m.nx + 1) * m.ny, S(0.0));
   for (int j = 0; j < m.ny; ++j) {
     for (int f = 0; f <= m.nx; ++f) {
       int iL = f - 1, iR = f;
-      S qL[4], qR[4];
-      for (int l = 0; l < 4; ++l) {
+      S qL[MAXF], qR[MAXF];
+      for (int l = 0; l < nf; ++l) {
         S sL = limiter(c, q_at(l, iL, j) - q_at(l, iL - 1, j), q_at(l, iL + 1, j) - q_at(l, iL, j));
         S sR = limiter(c, q_at(l, iR, j) - q_at(l, iR - 1, j), q_at(l, iR + 1, j) - q_at(l, iR, j));
         qL[l] = q_at(l, iL, j) + 0.5 * sL;
         qR[l] = q_at(l, iR, j) - 0.5 * sR;
       }
-      S F[4];
+      S F[MAXF];
       face_flux(c, 0, qL, qR, F);
-      for (int l = 0; l < 4; ++l) Fx[l][(size_t)j * (m.nx + 1) + f] = F[l];
+      for (int l = 0; l < nf; ++l) Fx[l][(size_t)j * (m.nx + 1) + f] = F[l];
     }
   }
   // y-faces
   if (c.dim == 2) {
-    for (int l = 0; l < 4; ++l) Fy[l].assign((size_t)m.nx * (m.ny + 1), S(0.0));
+    for (int l = 0; l < nf; ++l) Fy[l].assign((size_t)m.nx * (m.ny + 1), S(0.0));
     for (int g = 0; g <= m.ny; ++g) {
       for (int i = 0; i < m.nx; ++i) {
         int jL = g - 1, jR = g;
-        S qL[4], qR[4];
-        for (int l = 0; l < 4; ++l) {
+        S qL[MAXF], qR[MAXF];
+        for (int l = 0; l < nf; ++l) {
           S sL = limiter(c, q_at(l, i, jL) - q_at(l, i, jL - 1), q_at(l, i, jL + 1) - q_at(l, i, jL));
           S sR = limiter(c, q_at(l, i, jR) - q_at(l, i, jR - 1), q_at(l, i, jR + 1) - q_at(l, i, jR));
           qL[l] = q_at(l, i, jL) + 0.5 * sL;
           qR[l] = q_at(l, i, jR) - 0.5 * sR;
         }
-        S F[4];
+        S F[MAXF];
         face_flux(c, 1, qL, qR, F);
-        for (int l = 0; l < 4; ++l) Fy[l][(size_t)g * m.nx + i] = F[l];
+        for (int l = 0; l < nf; ++l) Fy[l][(size_t)g * m.nx + i] = F[l];
       }
     }
   }
@@ -317,11 +337,12 @@ S flux_balance(const Mesh<S>& m, const std::vector<S>& Fx, const std::vector<S>&
 }
 
 // Heun step 1 under the CFL reading stated at the top of this file.
-double cfl_dt(const OracleConfig& c, const std::vector<double> U[4]) {
+double cfl_dt(const OracleConfig& c, const std::vector<double> U[]) {
   double smax = 0.0;
   size_t n = (size_t)c.nx * c.ny;
   for (size_t k = 0; k < n; ++k) {
-    double Uc[4] = {U[0][k], U[1][k], U[2][k], U[3][k]}, q[4];
+    double Uc[MAXF], q[MAXF];
+    for (int l = 0; l < nfields(c); ++l) Uc[l] = U[l][k];
     prim_from_cons(c, Uc, q);
     double a = sound_speed(c, q[0], q[3]);
     double s = (std::fabs(q[1]) + a) / c.dx;
@@ -333,21 +354,22 @@ double cfl_dt(const OracleConfig& c, const std::vector<double> U[4]) {
 
 // One Heun step (Sec. 4, steps 2-11) with a given dt.
 template <class S>
-bool heun_step(const OracleConfig& c, std::vector<S> U[4], double dt) {
+bool heun_step(const OracleConfig& c, std::vector<S> U[], double dt) {
   Mesh<S> m(c);
-  std::vector<S> Fxn[4], Fyn[4], Fxs[4], Fys[4], Us[4];
+  const int nf = nfields(c);
+  std::vector<S> Fxn[MAXF], Fyn[MAXF], Fxs[MAXF], Fys[MAXF], Us[MAXF];
   bool ok = all_face_fluxes(m, U, Fxn, Fyn);  // steps 2-5
-  for (int l = 0; l < 4; ++l) Us[l].resize(m.ncell());
+  for (int l = 0; l < nf; ++l) Us[l].resize(m.ncell());
   for (int j = 0; j < m.ny; ++j)  // step 6: predicted states
     for (int i = 0; i < m.nx; ++i) {
       size_t k = (size_t)j * m.nx + i;
-      for (int l = 0; l < 4; ++l) Us[l][k] = U[l][k] - dt * flux_balance(m, Fxn[l], Fyn[l], i, j);
+      for (int l = 0; l < nf; ++l) Us[l][k] = U[l][k] - dt * flux_balance(m, Fxn[l], Fyn[l], i, j);
     }
   ok = all_face_fluxes(m, Us, Fxs, Fys) && ok;  // steps 7-10
   for (int j = 0; j < m.ny; ++j)  // step 11: averaged fluxes
     for (int i = 0; i < m.nx; ++i) {
       size_t k = (size_t)j * m.nx + i;
-      for (int l = 0; l < 4; ++l) {
+      for (int l = 0; l < nf; ++l) {
         S bn = flux_balance(m, Fxn[l], Fyn[l], i, j);
         S bs = flux_balance(m, Fxs[l], Fys[l], i, j);
         U[l][k] = U[l][k] - dt * ((bn + bs) / 2.0);
@@ -355,7 +377,8 @@ bool heun_step(const OracleConfig& c, std::vector<S> U[4], double dt) {
     }
   // Positivity of the new state.
   for (size_t k = 0; k < m.ncell(); ++k) {
-    S Uc[4] = {U[0][k], U[1][k], U[2][k], U[3][k]}, q[4];
+    S Uc[MAXF], q[MAXF];
+    for (int l = 0; l < nf; ++l) Uc[l] = U[l][k];
     prim_from_cons(c, Uc, q);
     if (!(val(q[0]) > 0.0) || !(val(q[3]) > 0.0)) ok = false;
   }
@@ -370,33 +393,35 @@ bool heun_step(const OracleConfig& c, std::vector<S> U[4], double dt) {
 //   U2 = 3/4 U^n + 1/4 (U1 + dt L(U1))
 //   U^{n+1} = 1/3 U^n + 2/3 (U2 + dt L(U2))
 template <class S>
-bool ssprk3_step(const OracleConfig& c, std::vector<S> U[4], double dt) {
+bool ssprk3_step(const OracleConfig& c, std::vector<S> U[], double dt) {
   Mesh<S> m(c);
-  std::vector<S> Fx[4], Fy[4], U1[4], U2[4];
+  const int nf = nfields(c);
+  std::vector<S> Fx[MAXF], Fy[MAXF], U1[MAXF], U2[MAXF];
   bool ok = all_face_fluxes(m, U, Fx, Fy);
-  for (int l = 0; l < 4; ++l) U1[l].resize(m.ncell());
+  for (int l = 0; l < nf; ++l) U1[l].resize(m.ncell());
   for (int j = 0; j < m.ny; ++j)
     for (int i = 0; i < m.nx; ++i) {
       size_t k = (size_t)j * m.nx + i;
-      for (int l = 0; l < 4; ++l) U1[l][k] = U[l][k] - dt * flux_balance(m, Fx[l], Fy[l], i, j);
+      for (int l = 0; l < nf; ++l) U1[l][k] = U[l][k] - dt * flux_balance(m, Fx[l], Fy[l], i, j);
     }
   ok = all_face_fluxes(m, U1, Fx, Fy) && ok;
-  for (int l = 0; l < 4; ++l) U2[l].resize(m.ncell());
+  for (int l = 0; l < nf; ++l) U2[l].resize(m.ncell());
   for (int j = 0; j < m.ny; ++j)
     for (int i = 0; i < m.nx; ++i) {
       size_t k = (size_t)j * m.nx + i;
-      for (int l = 0; l < 4; ++l)
+      for (int l = 0; l < nf; ++l)
         U2[l][k] = 0.75 * U[l][k] + 0.25 * (U1[l][k] - dt * flux_balance(m, Fx[l], Fy[l], i, j));
     }
   ok = all_face_fluxes(m, U2, Fx, Fy) && ok;
   for (int j = 0; j < m.ny; ++j)
     for (int i = 0; i < m.nx; ++i) {
       size_t k = (size_t)j * m.nx + i;
-      for (int l = 0; l < 4; ++l)
+      for (int l = 0; l < nf; ++l)
         U[l][k] = U[l][k] / 3.0 + (2.0 / 3.0) * (U2[l][k] - dt * flux_balance(m, Fx[l], Fy[l], i, j));
     }
   for (size_t k = 0; k < m.ncell(); ++k) {
-    S Uc[4] = {U[0][k], U[1][k], U[2][k], U[3][k]}, q[4];
+    S Uc[MAXF], q[MAXF];
+    for (int l = 0; l < nf; ++l) Uc[l] = U[l][k];
     prim_from_cons(c, Uc, q);
     if (!(val(q[0]) > 0.0) || !(val(q[3]) > 0.0)) ok = false;
   }
@@ -404,24 +429,25 @@ bool ssprk3_step(const OracleConfig& c, std::vector<S> U[4], double dt) {
 }
 
 template <class S>
-bool time_step(const OracleConfig& c, std::vector<S> U[4], double dt) {
+bool time_step(const OracleConfig& c, std::vector<S> U[], double dt) {
   return c.time_order == 3 ? ssprk3_step(c, U, dt) : heun_step(c, U, dt);
 }
 
-void load_planes(const OracleConfig& c, const double* src, std::vector<double> U[4]) {
+void load_planes(const OracleConfig& c, const double* src, std::vector<double> U[]) {
   size_t n = (size_t)c.nx * c.ny;
-  for (int l = 0; l < 4; ++l) U[l].assign(src + l * n, src + (l + 1) * n);
+  for (int l = 0; l < nfields(c); ++l) U[l].assign(src + l * n, src + (l + 1) * n);
 }
-void store_planes(const OracleConfig& c, const std::vector<double> U[4], double* dst) {
+void store_planes(const OracleConfig& c, const std::vector<double> U[], double* dst) {
   size_t n = (size_t)c.nx * c.ny;
-  for (int l = 0; l < 4; ++l) std::memcpy(dst + l * n, U[l].data(), n * sizeof(double));
+  for (int l = 0; l < nfields(c); ++l) std::memcpy(dst + l * n, U[l].data(), n * sizeof(double));
 }
 
 }  // namespace
 
 // ===========================================================================
-// C entry points used through ctypes.  Arrays of 4 planes are stored plane
-// after plane (rho, rho u, rho v, rho E), each plane nx*ny values, x fastest.
+// C entry points used through ctypes.  A state is nfields = 4 + nspecies
+// planes stored plane after plane (rho, rho u, rho v, rho E, rho y_1 ..), each
+// plane nx*ny values, x fastest.
 // Return ORC_OK, ORC_NONPHYSICAL (a non-positive density or pressure met) or
 // ORC_ARG (invalid configuration or argument).
 // ===========================================================================
@@ -443,21 +469,24 @@ int oracle_interface_solve(const OracleConfig* c, int64_t n, const double* L, co
   return ORC_OK;
 }
 
-// qL, qR, F are n x 4 arrays; q = (rho, u, v, p).
+// qL, qR, F are n x nfields arrays; q = (rho, u, v, p, y_1 ..).
 int oracle_face_flux(const OracleConfig* c, int dir, int64_t n, const double* qL, const double* qR,
                      double* F) {
-  if (!c || n < 0 || (dir != 0 && dir != 1)) return ORC_ARG;
-  for (int64_t k = 0; k < n; ++k) face_flux(*c, dir, qL + 4 * k, qR + 4 * k, F + 4 * k);
+  if (!c || n < 0 || (dir != 0 && dir != 1) || c->nspecies < 0 || c->nspecies > MAX_SPECIES) return ORC_ARG;
+  const int nf = nfields(*c);
+  for (int64_t k = 0; k < n; ++k) face_flux(*c, dir, qL + nf * k, qR + nf * k, F + nf * k);
   return ORC_OK;
 }
 
 int oracle_prim_to_cons(const OracleConfig* c, const double* q, double* U) {
   if (!config_ok(c)) return ORC_ARG;
   size_t n = (size_t)c->nx * c->ny;
+  const int nf = nfields(*c);
   for (size_t k = 0; k < n; ++k) {
-    double qc[4] = {q[k], q[n + k], q[2 * n + k], q[3 * n + k]}, Uc[4];
+    double qc[MAXF] = {}, Uc[MAXF];
+    for (int l = 0; l < nf; ++l) qc[l] = q[l * n + k];
     cons_from_prim(*c, qc, Uc);
-    for (int l = 0; l < 4; ++l) U[l * n + k] = Uc[l];
+    for (int l = 0; l < nf; ++l) U[l * n + k] = Uc[l];
   }
   return ORC_OK;
 }
@@ -465,17 +494,19 @@ int oracle_prim_to_cons(const OracleConfig* c, const double* q, double* U) {
 int oracle_cons_to_prim(const OracleConfig* c, const double* U, double* q) {
   if (!config_ok(c)) return ORC_ARG;
   size_t n = (size_t)c->nx * c->ny;
+  const int nf = nfields(*c);
   for (size_t k = 0; k < n; ++k) {
-    double Uc[4] = {U[k], U[n + k], U[2 * n + k], U[3 * n + k]}, qc[4];
+    double Uc[MAXF] = {}, qc[MAXF];
+    for (int l = 0; l < nf; ++l) Uc[l] = U[l * n + k];
     prim_from_cons(*c, Uc, qc);
-    for (int l = 0; l < 4; ++l) q[l * n + k] = qc[l];
+    for (int l = 0; l < nf; ++l) q[l * n + k] = qc[l];
   }
   return ORC_OK;
 }
 
 int oracle_dt(const OracleConfig* c, const double* Uin, double* dt) {
   if (!config_ok(c) || !Uin || !dt) return ORC_ARG;
-  std::vector<double> U[4];
+  std::vector<double> U[MAXF];
   load_planes(*c, Uin, U);
   *dt = cfl_dt(*c, U);
   return ORC_OK;
@@ -485,14 +516,14 @@ int oracle_dt(const OracleConfig* c, const double* Uin, double* dt) {
 // scheme after eq. (11).
 int oracle_residual(const OracleConfig* c, const double* Uin, double* LU) {
   if (!config_ok(c) || !Uin || !LU) return ORC_ARG;
-  std::vector<double> U[4], Fx[4], Fy[4];
+  std::vector<double> U[MAXF], Fx[MAXF], Fy[MAXF];
   load_planes(*c, Uin, U);
   Mesh<double> m(*c);
   bool ok = all_face_fluxes(m, U, Fx, Fy);
   size_t n = m.ncell();
   for (int j = 0; j < m.ny; ++j)
     for (int i = 0; i < m.nx; ++i)
-      for (int l = 0; l < 4; ++l)
+      for (int l = 0; l < nfields(*c); ++l)
         LU[l * n + (size_t)j * m.nx + i] = -flux_balance(m, Fx[l], Fy[l], i, j);
   return ok ? ORC_OK : ORC_NONPHYSICAL;
 }
@@ -505,7 +536,7 @@ int oracle_residual(const OracleConfig* c, const double* Uin, double* LU) {
 int oracle_run(const OracleConfig* c, double* Uio, int32_t max_steps, double t0, double t_end,
                const double* dts_in, double* dts_out, int32_t* steps_done, double* t_out) {
   if (!config_ok(c) || !Uio || max_steps < 0) return ORC_ARG;
-  std::vector<double> U[4];
+  std::vector<double> U[MAXF];
   load_planes(*c, Uio, U);
   double t = t0;
   int n = 0;
@@ -530,25 +561,26 @@ int oracle_run(const OracleConfig* c, double* Uio, int32_t max_steps, double t0,
 }
 
 // Forward-mode directional derivative of nsteps Heun steps with the frozen
-// dt sequence dts.  q0 and dq0 are the initial primitive planes (rho, u, v, p)
-// and their tangent; U_out and dU_out receive the final conservative planes
-// and their tangent.
+// dt sequence dts.  q0 and dq0 are the initial primitive planes (rho, u, v, p,
+// y_1 ..) and their tangent; U_out and dU_out receive the final conservative
+// planes and their tangent.
 int oracle_run_tangent(const OracleConfig* c, const double* q0, const double* dq0, int32_t nsteps,
                        const double* dts, double* U_out, double* dU_out) {
   if (!config_ok(c) || !q0 || !dq0 || !dts || nsteps < 0) return ORC_ARG;
   size_t n = (size_t)c->nx * c->ny;
-  std::vector<Dual> U[4];
-  for (int l = 0; l < 4; ++l) U[l].resize(n);
+  const int nf = nfields(*c);
+  std::vector<Dual> U[MAXF];
+  for (int l = 0; l < nf; ++l) U[l].resize(n);
   for (size_t k = 0; k < n; ++k) {
-    Dual qc[4], Uc[4];
-    for (int l = 0; l < 4; ++l) qc[l] = Dual(q0[l * n + k], dq0[l * n + k]);
+    Dual qc[MAXF], Uc[MAXF];
+    for (int l = 0; l < nf; ++l) qc[l] = Dual(q0[l * n + k], dq0[l * n + k]);
     cons_from_prim(*c, qc, Uc);
-    for (int l = 0; l < 4; ++l) U[l][k] = Uc[l];
+    for (int l = 0; l < nf; ++l) U[l][k] = Uc[l];
   }
   int status = ORC_OK;
   for (int s = 0; s < nsteps; ++s)
     if (!time_step(*c, U, dts[s])) status = ORC_NONPHYSICAL;
-  for (int l = 0; l < 4; ++l)
+  for (int l = 0; l < nf; ++l)
     for (size_t k = 0; k < n; ++k) {
       U_out[l * n + k] = U[l][k].v;
       dU_out[l * n + k] = U[l][k].d;

@@ -6,13 +6,18 @@ checked against.  Only tests, the smoke check and the CPU-baseline leg of the
 benchmark may import this module; the product package never does.
 
 Arrays use the oracle's own layout: a state is a float64 array of shape
-(4, ny, nx) holding (rho, rho u, rho v, rho E) -- or (rho, u, v, p) for
-primitive states -- with x fastest.  1D problems have ny == 1.
+(4 + nspecies, ny, nx) holding (rho, rho u, rho v, rho E, rho y_1 ..) -- or
+(rho, u, v, p, y_1 ..) for primitive states -- with x fastest.  1D problems
+have ny == 1.
 
 Parity status of each function (see the pins in tests/test_oracle_*.py):
   limiter, interface_solve, face_flux, prim/cons, dt, residual, run,
   run_tangent -- all pinned (closed forms, invariants, exact Riemann
-  solutions, convergence order, finite differences).  The scheme's exact
+  solutions, convergence order, finite differences).  Species transport
+  (nspecies > 0, Sec. 5) is pinned by the constant-fraction and
+  complementary-fraction invariants, bitwise independence of the gas
+  dynamics, second-order convergence of uniform-flow advection to the exact
+  translation and the maximum principle (tests/test_oracle_species.py).  The scheme's exact
   numerical values on the paper's shock tubes are not printed in the paper
   (figures lost), so no stored value pins them; the invariants above do.
 """
@@ -52,7 +57,7 @@ class _Cfg(ctypes.Structure):
         ("cfl", ctypes.c_double),
         ("beta", ctypes.c_double),
         ("time_order", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("nspecies", ctypes.c_int32),
     ]
 
 
@@ -72,13 +77,18 @@ class OracleConfig:
     lx: float = 1.0
     ly: float = 1.0
     time_order: int = 2  # 2: Heun (Sec. 4), 3: third-order SSP Runge-Kutta
+    nspecies: int = 0  # transported mass fractions y_k (Sec. 5)
+
+    @property
+    def nfields(self) -> int:
+        return 4 + self.nspecies
 
     def to_c(self) -> _Cfg:
         ny = self.ny if self.dim == 2 else 1
         return _Cfg(
             self.dim, self.nx, ny, LIMITERS[self.limiter], BCS[self.bc], RIEMANN[self.riemann],
             self.lx / self.nx, self.ly / ny if self.dim == 2 else 1.0, self.gamma, self.cfl, self.beta,
-            self.time_order, 0,
+            self.time_order, self.nspecies,
         )
 
 
@@ -194,8 +204,10 @@ def interface_solve(cfg: OracleConfig, L, R):
 
 
 def face_flux(cfg: OracleConfig, direction: int, qL, qR) -> np.ndarray:
-    """qL, qR: (..., 4) primitive face states (rho, u, v, p).  Returns (..., 4) fluxes."""
-    qL, qR = _f64(qL).reshape(-1, 4), _f64(qR).reshape(-1, 4)
+    """qL, qR: (..., nfields) primitive face states (rho, u, v, p, y_1 ..).
+    Returns (..., nfields) fluxes."""
+    nf = cfg.nfields
+    qL, qR = _f64(qL).reshape(-1, nf), _f64(qR).reshape(-1, nf)
     F = np.empty_like(qL)
     c = cfg.to_c()
     _check(_load().oracle_face_flux(ctypes.byref(c), direction, len(qL), _ptr(qL), _ptr(qR), _ptr(F)))
@@ -208,8 +220,8 @@ def face_flux(cfg: OracleConfig, direction: int, qL, qR) -> np.ndarray:
 def _state(cfg: OracleConfig, U) -> np.ndarray:
     U = _f64(U)
     ny = cfg.ny if cfg.dim == 2 else 1
-    if U.shape != (4, ny, cfg.nx):
-        U = U.reshape(4, ny, cfg.nx)
+    if U.shape != (cfg.nfields, ny, cfg.nx):
+        U = U.reshape(cfg.nfields, ny, cfg.nx)
     return np.ascontiguousarray(U)
 
 
@@ -276,7 +288,7 @@ def run(cfg: OracleConfig, U0, max_steps: int, t_end: float = 0.0, t0: float = 0
 def run_tangent(cfg: OracleConfig, q0, dq0, dts):
     """Forward-mode (dual number) derivative of len(dts) steps with frozen dt.
 
-    q0, dq0: primitive initial planes (rho, u, v, p) and a tangent direction.
+    q0, dq0: primitive initial planes (rho, u, v, p, y_1 ..) and a tangent direction.
     Returns (U_T, dU_T): final conservative state and its directional derivative.
     """
     q0, dq0 = _state(cfg, q0), _state(cfg, dq0)

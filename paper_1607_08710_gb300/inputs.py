@@ -1,10 +1,10 @@
 """Seeded synthetic initial conditions.
 
-This module only draws and lays out primitive fields (rho, u, v, p) on cell
-centres; it holds none of the scheme's arithmetic (no equation of state, no
-flux), so that the CUDA path and the CPU oracle can both start from exactly the
-same input.  Every array is float64 with shape (ny, nx), x fastest; 1D
-problems have ny == 1.
+This module only draws and lays out primitive fields (rho, u, v, p, and
+optionally mass fractions y_k) on cell centres; it holds none of the scheme's
+arithmetic (no equation of state, no flux), so that the CUDA path and the CPU
+oracle can both start from exactly the same input.  Every array is float64
+with shape (ny, nx), x fastest; 1D problems have ny == 1.
 
 Workloads:
   * shock tubes of Sec. 4.2 (Sod, two-rarefaction, sonic rarefaction,
@@ -13,7 +13,11 @@ Workloads:
   * a smooth density wave rho = 1 + 0.2 sin(2 pi (x + y)), u = v = 0.5, p = 1,
     whose exact solution is a translation;
   * a seeded Kelvin-Helmholtz shear layer;
-  * seeded mesh sizes for batches of independent problems.
+  * seeded mesh sizes for batches of independent problems;
+  * transported mass fractions (Sec. 5): a smooth scalar carried by a uniform
+    flow (exact solution: a translation), a seeded three-region, two-material
+    problem on the (0, 7) x (0, 3) vessel of the paper's triple-point case,
+    and material indicators of the shear layer.
 """
 from __future__ import annotations
 
@@ -39,9 +43,18 @@ class Primitive:
     u: np.ndarray
     v: np.ndarray
     p: np.ndarray
+    y: np.ndarray | None = None  # mass fractions, shape (nspecies, ny, nx)
+
+    @property
+    def nspecies(self) -> int:
+        return 0 if self.y is None else int(self.y.shape[0])
 
     def stack(self) -> np.ndarray:
-        return np.stack([self.rho, self.u, self.v, self.p]).astype(np.float64)
+        """(4 + nspecies, ny, nx): rho, u, v, p, then y_1 .. y_nspecies."""
+        planes = [self.rho, self.u, self.v, self.p]
+        if self.y is not None:
+            planes += list(self.y)
+        return np.stack(planes).astype(np.float64)
 
     @property
     def shape(self):
@@ -164,3 +177,90 @@ def batched_sizes(nprob: int, seed: int = 0, lo: int = 64, hi: int = 1024) -> np
         out[k, 0] = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
         out[k, 1] = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
     return out
+
+
+def with_species(prim: Primitive, y) -> Primitive:
+    """The same flow carrying the mass fractions y (shape (nspecies, ny, nx))."""
+    y = np.asarray(y, dtype=np.float64)
+    if y.ndim == 2:
+        y = y[None]
+    assert y.shape[1:] == prim.shape
+    return Primitive(prim.rho, prim.u, prim.v, prim.p, y.copy())
+
+
+def advected_scalar_1d(nx: int, t: float = 0.0) -> Primitive:
+    """rho = 1, u = 1, p = 1 on the periodic unit interval carrying
+    y = 0.5 + 0.4 sin(2 pi (x - t)): the exact solution at time t."""
+    x = cell_centres(nx)[None, :]
+    one = np.ones((1, nx))
+    y = 0.5 + 0.4 * np.sin(2.0 * math.pi * (x - t))
+    return Primitive(one.copy(), one.copy(), np.zeros((1, nx)), one.copy(), y[None])
+
+
+def advected_scalar(nx: int, ny: int | None = None, t: float = 0.0) -> Primitive:
+    """rho = 1, u = v = 0.5, p = 1 on the periodic unit square carrying
+    y = 0.5 + 0.4 sin(2 pi (x + y - t)): the exact solution at time t."""
+    ny = nx if ny is None else ny
+    x = cell_centres(nx)[None, :]
+    yc = cell_centres(ny)[:, None]
+    one = np.ones((ny, nx))
+    y = 0.5 + 0.4 * np.sin(2.0 * math.pi * (x + yc - t))
+    return Primitive(one.copy(), 0.5 * one, 0.5 * one, one.copy(), y[None])
+
+
+def advected_indicator(nx: int, ny: int | None = None) -> Primitive:
+    """rho = 1, u = 0.6, v = -0.3, p = 1 (periodic unit square) carrying the
+    indicator of the disc |(x, y) - (0.4, 0.6)| < 0.2."""
+    ny = nx if ny is None else ny
+    x = cell_centres(nx)[None, :]
+    yc = cell_centres(ny)[:, None]
+    one = np.ones((ny, nx))
+    y = ((x - 0.4) ** 2 + (yc - 0.6) ** 2 < 0.04).astype(np.float64)
+    return Primitive(one.copy(), 0.6 * one, -0.3 * one, one.copy(), y[None])
+
+
+TRIPLE_DOMAIN = (7.0, 3.0)  # the vessel (0, 7) x (0, 3) of the triple-point case
+
+
+def three_region_states(seed: int) -> np.ndarray:
+    """Three resting states, rows for regions 1, 2, 3, columns (rho, p):
+    rho ~ U[0.1, 1.0], p ~ U[0.1, 1.0], drawn region by region (rho, then p)."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((3, 2))
+    for r in range(3):
+        out[r, 0] = rng.uniform(0.1, 1.0)
+        out[r, 1] = rng.uniform(0.1, 1.0)
+    return out
+
+
+def three_region(nx: int, ny: int, seed: int = 0) -> Primitive:
+    """Three-state, two-material problem on (0, 7) x (0, 3) at rest.
+
+    Region 1 is x < 1, region 2 is x > 1, y < 1.5 and region 3 is x > 1,
+    y > 1.5 (the layout of the triple-point case of Sec. 5; its geometry
+    figure is not part of the text, so the split lines are this module's
+    choice).  States are seeded.  Material A fills regions 1 and 3 and
+    material B region 2; y_1 and y_2 are their indicators (y_1 + y_2 = 1).
+    """
+    lx, ly = TRIPLE_DOMAIN
+    st = three_region_states(seed)
+    x = cell_centres(nx, 0.0, lx)[None, :] * np.ones((ny, 1))
+    yc = cell_centres(ny, 0.0, ly)[:, None] * np.ones((1, nx))
+    region = np.where(x < 1.0, 0, np.where(yc < 1.5, 1, 2))
+    zero = np.zeros((ny, nx))
+    yA = (region != 1).astype(np.float64)
+    return Primitive(st[region, 0], zero.copy(), zero.copy(), st[region, 1], np.stack([yA, 1.0 - yA]))
+
+
+def shear_layer_tracers(nx: int, ny: int | None = None, seed: int = 0, nspecies: int = 2) -> Primitive:
+    """The Kelvin-Helmholtz shear layer carrying nspecies mass fractions: y_1 is
+    the indicator of the layer |y - 0.5| < 0.25, y_2 = 1 - y_1, and further
+    species (if any) are smooth seeded fields in [0.1, 0.9]."""
+    ny = nx if ny is None else ny
+    kh = kelvin_helmholtz(nx, ny, seed=seed)
+    yc = cell_centres(ny)[:, None] * np.ones((1, nx))
+    inside = (np.abs(yc - 0.5) < 0.25).astype(np.float64)
+    ys = [inside, 1.0 - inside]
+    for k in range(2, nspecies):
+        ys.append(0.5 + 0.4 * smooth_perturbation(nx, ny, seed=seed * 31 + k))
+    return with_species(kh, np.stack(ys[:nspecies]))

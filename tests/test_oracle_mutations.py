@@ -36,6 +36,11 @@ MUTANTS = {
     "dt_without_y": ("if (c.dim == 2) s += (std::fabs(q[2]) + a) / c.dy;", ""),
     "momentum_pressure_wrong_axis": ("F[1 + dir] = F[1 + dir] + pstar;", "F[1] = F[1] + pstar;"),
     "rk3_stage2_weight": ("U2[l][k] = 0.75 * U[l][k] + 0.25 *", "U2[l][k] = 0.70 * U[l][k] + 0.30 *"),
+    "species_fraction_not_divided": ("q[4 + k] = U[4 + k] / rho;", "q[4 + k] = U[4 + k];"),
+    "species_cons_without_rho": ("U[4 + k] = rho * q[4 + k];", "U[4 + k] = q[4 + k];"),
+    "species_fraction_of_wrong_species": ("q[4 + k] = U[4 + k] / rho;", "q[4 + k] = U[4 + c.nspecies - 1 - k] / rho;"),
+    "species_update_skips_last": ("for (int l = 0; l < nf; ++l) Us[l][k] = U[l][k] - dt",
+                                  "for (int l = 0; l < nf - (nf > 4); ++l) Us[l][k] = U[l][k] - dt"),
 }
 
 
@@ -120,6 +125,33 @@ def battery():
     ref = U3 + dt * (k1 / 6 + k2 / 6 + 2 * k3 / 3)
     got = O.run(c3, U3, 1, dts=[dt], allow_nonphysical=True).U
     check("rk3_butcher", np.allclose(got, ref, rtol=1e-12, atol=1e-13))
+    # species: a constant fraction stays constant; y_2 = 1 - y_1 keeps summing
+    # to one; uniform-flow advection of y converges at second order
+    cs = O.OracleConfig(nx=12, ny=9, nspecies=2)
+    ps = inputs.quadrant(12, 9, seed=2)
+    ys = np.stack([np.full((9, 12), 0.3), np.random.default_rng(1).uniform(0, 1, (9, 12))])
+    ys[1] = np.where(ys[1] > 0.5, 1.0, 0.0)
+    try:
+        Us = O.run(cs, O.prim_to_cons(cs, np.concatenate([ps.stack(), ys])), 6, allow_nonphysical=True).U
+        check("species_constant", np.abs(Us[4] - 0.3 * Us[0]).max() < 1e-13)
+    except O.OracleError:
+        check("species_constant", False)
+    c2 = O.OracleConfig(nx=40, ny=20, lx=7.0, ly=3.0, nspecies=2)
+    try:
+        U2s = O.run(c2, O.prim_to_cons(c2, inputs.three_region(40, 20, seed=1).stack()), 8, allow_nonphysical=True).U
+        check("species_sum", np.abs(U2s[4] + U2s[5] - U2s[0]).max() < 1e-13)
+    except O.OracleError:
+        check("species_sum", False)
+    es = []
+    for m in (64, 128):
+        ca = O.OracleConfig(nx=m, dim=1, bc="periodic", nspecies=1, cfl=0.4)
+        try:
+            ra = O.run(ca, O.prim_to_cons(ca, inputs.advected_scalar_1d(m).stack()), 10**5, t_end=0.25,
+                       allow_nonphysical=True)
+            es.append(np.abs(ra.U[4, 0] / ra.U[0, 0] - inputs.advected_scalar_1d(m, t=0.25).y[0, 0]).mean())
+        except O.OracleError:
+            es.append(np.inf)
+    check("species_order2", np.all(np.isfinite(es)) and es[1] > 0 and math.log2(es[0] / es[1]) > 1.75)
     return fails
 
 
