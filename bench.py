@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-rk3", action="store_true")
     ap.add_argument("--rk3-steps", type=int, default=100)
+    ap.add_argument("--no-species", action="store_true")
+    ap.add_argument("--species-steps", type=int, default=100)
     ap.add_argument("--batch-problems", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=300)
     return ap.parse_args()
@@ -435,6 +437,50 @@ def run_ours(args, dist):
         out["rk3"] = {"value": cells * args.rk3_steps / t3, "unit": METRIC, "steps": args.rk3_steps,
                       "ms_per_step": 1e3 * t3 / args.rk3_steps, "first_stage_ms": a0 / c0,
                       "later_stage_ms": a1 / c1, "integrator": "SSP-RK3 (Shu-Osher), 3 fused stages per step"}
+        torch.cuda.empty_cache()
+
+    # the same shear layer carrying two transported mass fractions (Sec. 5): 6 fields per cell
+    if not args.no_species and dist.rank == 0:
+        ns = 2
+        ps = inputs.shear_layer_tracers(n, n, seed=0, nspecies=ns).stack()
+        ssp = LagrangeFlux(Config(precision=prec, nspecies=ns, **kw))
+        q = torch.from_numpy(ps).to(dev, tdt)
+        del ps
+        ssp.set_primitive(q[0], q[1], q[2], q[3])
+        ssp.set_mass_fractions(q[4:].contiguous())
+        del q
+        for _ in range(args.warmup):
+            ssp.step()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.species_steps):
+            ssp.step()
+        e1.record()
+        torch.cuda.synchronize()
+        tsp = e0.elapsed_time(e1) / 1e3
+        ssp.sync()
+        ssp.profile(True)
+        for _ in range(args.profile_steps):
+            ssp.step()
+        (a0, a1), (c0, c1) = ssp.profile_read()
+        ssp.close()
+        word = 4 if prec == "fp32" else 8
+        nf = 4 + ns
+        ms = {"stage0": a0 / c0, "stage1": a1 / c1}
+        byts = {"stage0": 2 * nf * word * cells, "stage1": 3 * nf * word * cells}
+        peak, peak_kind = peaks()
+        sk = max(ms, key=ms.get)
+        gbs = byts[sk] / (ms[sk] / 1e3) / 1e9
+        out["species"] = {
+            "value": cells * args.species_steps / tsp, "unit": METRIC, "steps": args.species_steps,
+            "ms_per_step": 1e3 * tsp / args.species_steps, "nspecies": ns, "stage_ms": [ms["stage0"], ms["stage1"]],
+            "roofline": {"bound": "hbm", "kernel": f"stage2d_kernel<{'float' if prec == 'fp32' else 'double'}, "
+                         f"VANLEER, {'predictor' if sk == 'stage0' else 'corrector'}, NF={nf}>",
+                         "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "peak_kind": f"{peak_kind} copy bandwidth",
+                         "algorithmic_bytes_per_cell": byts[sk] // cells},
+            "workload": f"periodic shear layer {n}x{n} with tracers y_1 = layer indicator, y_2 = 1 - y_1"}
         torch.cuda.empty_cache()
 
     # batched: 512 seeded uneven meshes, one persistent launch per stage, graph of the step loop

@@ -7,7 +7,10 @@
  * primitive variables with a limited slope (eq. "sweby"), the Lagrangian
  * HLL / acoustic interface solver (Sec. 4.1, eqs. 13-14), the upwind
  * Lagrange flux (eq. 12) and the two-stage Heun time integrator (Sec. 4,
- * steps 1-11) under a CFL time step.
+ * steps 1-11) under a CFL time step.  A state may also carry up to
+ * LF_MAX_SPECIES transported mass fractions y_k (Sec. 5: the conservative
+ * form d(rho y_k)/dt + div(rho y_k u) = 0), reconstructed and upwinded with
+ * the gas state by the same Lagrange flux.
  *
  * Conventions shared by every entry point:
  *   - Mesh: a uniform Cartesian mesh of nx x ny cells on
@@ -16,6 +19,8 @@
  *     (element (i, j) at index j*nx + i), of the configured precision:
  *     double for LF_FP64, float for LF_FP32.  The conservative planes are
  *     (rho, rho u, rho v, rho E); the primitive planes (rho, u, v, p).
+ *     Species planes (nspecies > 0) are passed as one buffer of nspecies
+ *     consecutive planes: partial densities rho y_k or mass fractions y_k.
  *   - Ownership: the caller owns every buffer it passes and keeps it; the
  *     library copies in and out and never retains a caller pointer.  The
  *     context owns its device state, scratch and scalars.
@@ -74,6 +79,8 @@ enum { LF_RIEMANN_MAXC = 0, LF_RIEMANN_PER_SIDE = 1 };
  * U' = 1/3 U + 2/3 (U2 + dt L(U2)).  SSP-RK3 needs one more state buffer and
  * is offered by lf_init contexts only. */
 enum { LF_TIME_HEUN = 2, LF_TIME_SSPRK3 = 3 };
+/* Largest number of transported mass fractions (lf_config.nspecies). */
+#define LF_MAX_SPECIES 2
 
 typedef struct lf_config {
   int32_t dim;       /* 1 or 2 */
@@ -84,7 +91,9 @@ typedef struct lf_config {
   int32_t riemann;   /* LF_RIEMANN_* */
   int32_t device;    /* CUDA device ordinal */
   int32_t time_order; /* LF_TIME_* (0 = LF_TIME_HEUN) */
-  int32_t reserved;  /* must be 0 */
+  int32_t nspecies;  /* transported mass fractions, 0 .. LF_MAX_SPECIES (Sec. 5);
+                        lf_init contexts only (0 for batches, the adjoint and
+                        lf_step_noalloc) */
   double xmin, xmax; /* domain in x */
   double ymin, ymax; /* domain in y (ignored in 1D) */
   double gamma;      /* ratio of specific heats, 1 < gamma <= 3 (Sec. 3) */
@@ -95,8 +104,9 @@ typedef struct lf_config {
 typedef struct lf_ctx lf_ctx;
 
 /* Creates a solver for one mesh.  `stream` is a cudaStream_t (NULL: default
- * stream).  Allocates the device state (4 planes), one intermediate Heun
- * state (4 planes) and a few scalars.  *out is set only on LF_OK. */
+ * stream).  Allocates the device state (4 + nspecies planes), one
+ * intermediate Heun state (as many planes; two for SSP-RK3) and a few
+ * scalars.  The species planes start at 0.  *out is set only on LF_OK. */
 lf_status lf_init(const lf_config* cfg, void* stream, lf_ctx** out);
 
 /* Frees everything the context owns.  NULL is ignored. */
@@ -104,7 +114,8 @@ void lf_destroy(lf_ctx* ctx);
 
 /* Copies in a conservative state (rho, rho u, rho v, rho E); in 1D rhov may
  * be NULL (taken as 0).  Resets t to 0 and the step count to 0 and computes
- * the wave-speed maximum for the first dt (Sec. 4, Heun step 1). */
+ * the wave-speed maximum for the first dt (Sec. 4, Heun step 1).  The
+ * species planes are left as they are. */
 lf_status lf_set_state(lf_ctx* ctx, const void* rho, const void* rhou, const void* rhov,
                        const void* rhoE, int on_device);
 
@@ -119,6 +130,18 @@ lf_status lf_get_state(lf_ctx* ctx, void* rho, void* rhou, void* rhov, void* rho
 
 /* Copies out the current primitive state (rho, u, v, p) via eq. (1). */
 lf_status lf_get_primitive(lf_ctx* ctx, void* rho, void* u, void* v, void* p, int on_device);
+
+/* Species (Sec. 5), for contexts with nspecies > 0 (LF_ERR_ARG otherwise).
+ * Partial densities: rho_y holds nspecies planes of rho y_k, copied in or
+ * out as they are.  Mass fractions: y holds nspecies planes of y_k; setting
+ * stores rho y_k = rho * y_k with the density of the current state (so call
+ * it after lf_set_state / lf_set_primitive), getting returns
+ * (rho y_k) / rho.  The species never enter the pressure, the sound speed or
+ * dt, so none of these calls touches t, the step count or the dt scalars. */
+lf_status lf_set_partial_densities(lf_ctx* ctx, const void* rho_y, int on_device);
+lf_status lf_get_partial_densities(lf_ctx* ctx, void* rho_y, int on_device);
+lf_status lf_set_mass_fractions(lf_ctx* ctx, const void* y, int on_device);
+lf_status lf_get_mass_fractions(lf_ctx* ctx, void* y, int on_device);
 
 /* One Heun step (Sec. 4, steps 1-11) with the CFL time step
  * dt = cfl / max_K[(|u|+c)/dx + (|v|+c)/dy]  (1D: cfl / max_K[(|u|+c)/dx]).
@@ -140,9 +163,11 @@ lf_status lf_run(lf_ctx* ctx, double t_end, int32_t max_steps, int32_t* steps_do
 /* Current time and completed step count (synchronises). */
 lf_status lf_get_time(lf_ctx* ctx, double* t, int64_t* steps);
 
-/* Compensated (Neumaier) FP64 sums of the four conservative fields over all
- * cells, in a fixed (deterministic) reduction order.  out[4]; synchronises. */
-lf_status lf_conservation_sums(lf_ctx* ctx, double out[4]);
+/* Compensated (Neumaier) FP64 sums of the 4 + nspecies conservative fields
+ * (rho, rho u, rho v, rho E, rho y_k) over all cells, in a fixed
+ * (deterministic) reduction order.  out holds 4 + nspecies doubles;
+ * synchronises. */
+lf_status lf_conservation_sums(lf_ctx* ctx, double* out);
 
 /* Waits for the context's stream and reports any device-side error flag. */
 lf_status lf_sync(lf_ctx* ctx);

@@ -37,6 +37,7 @@ const char* adjoint_unsupported(const lf_ctx* c) {
   if (c->cfg.dim != 2) return "the adjoint is implemented for 2D meshes";
   if (c->cfg.riemann != LF_RIEMANN_MAXC) return "the adjoint is implemented for the eqs. 13-14 solver (max c)";
   if (c->cfg.time_order == LF_TIME_SSPRK3) return "the adjoint is implemented for the Heun time integrator";
+  if (c->cfg.nspecies != 0) return "the adjoint is implemented for the gas dynamics without species";
   return nullptr;
 }
 

@@ -54,7 +54,7 @@ const char* validate(const lf_config* c) {
   if (c->limiter == LF_LIMITER_SWEBY && !(c->beta >= 1.0 && c->beta <= 2.0)) return "beta must be in [1, 2]";
   if (c->time_order != 0 && c->time_order != LF_TIME_HEUN && c->time_order != LF_TIME_SSPRK3)
     return "time_order must be 0, 2 (Heun) or 3 (SSP-RK3)";
-  if (c->reserved != 0) return "reserved must be 0";
+  if (c->nspecies < 0 || c->nspecies > LF_MAX_SPECIES) return "nspecies must be in [0, LF_MAX_SPECIES]";
   return nullptr;
 }
 
@@ -261,6 +261,9 @@ lf_status lf_init(const lf_config* cfg, void* stream, lf_ctx** out) {
   m.rdx = cfg->nx / (cfg->xmax - cfg->xmin);
   m.rdy = cfg->dim == 2 ? cfg->ny / (cfg->ymax - cfg->ymin) : 0.0;
   m.vec = 1;  // pitch is a multiple of 128 bytes and the planes come from cudaMalloc
+  m.nspecies = cfg->nspecies;
+  static_assert(LF_MAX_SPECIES == lf::MAX_SPECIES, "public and kernel species limits agree");
+  const int nf = 4 + cfg->nspecies;
 
   DeviceGuard g(cfg->device);
   if (!g.ok) {
@@ -268,14 +271,14 @@ lf_status lf_init(const lf_config* cfg, void* stream, lf_ctx** out) {
     delete c;
     return LF_ERR_CUDA;
   }
-  const size_t state_bytes = 4 * (size_t)m.plane * c->elem;
+  const size_t state_bytes = nf * (size_t)m.plane * c->elem;
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc(&c->U, state_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&c->Ustar, state_bytes);
   if (e == cudaSuccess && cfg->time_order == LF_TIME_SSPRK3) e = cudaMalloc(&c->U2, state_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&c->sc, sizeof(lf::Scalars));
-  if (e == cudaSuccess) e = cudaMalloc(&c->partials, (size_t)lf::sums_blocks() * 4 * 2 * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&c->dsums, 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->partials, (size_t)lf::sums_blocks() * nf * 2 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->dsums, nf * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&c->hsc, sizeof(lf::Scalars));
   if (e == cudaSuccess) e = lf::launch_reset_scalars(c->sc, cfg->cfl, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->U, 0, state_bytes, c->stream);
@@ -382,6 +385,92 @@ lf_status lf_get_primitive(lf_ctx* c, void* rho, void* u, void* v, void* p, int 
   if (!on_device) {
     for (int l = 0; l < 4; ++l)
       if (dst[l]) LF_CUDA(c, cudaMemcpyAsync(dst[l], kdst[l], n * c->elem, cudaMemcpyDeviceToHost, c->stream));
+    LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return LF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+lf_status species_args(lf_ctx* c, const void* p, const char* who) {
+  if (c->mesh.nspecies == 0) {
+    set_err(c, "%s: the context carries no species (nspecies == 0)", who);
+    return LF_ERR_ARG;
+  }
+  if (!p) {
+    set_err(c, "%s: NULL buffer", who);
+    return LF_ERR_ARG;
+  }
+  return LF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lf_status lf_set_partial_densities(lf_ctx* c, const void* rho_y, int on_device) {
+  if (!c) return LF_ERR_ARG;
+  if (lf_status st = species_args(c, rho_y, "lf_set_partial_densities")) return st;
+  DeviceGuard g(c->cfg.device);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const size_t n = (size_t)c->mesh.nx * c->mesh.ny;
+  for (int k = 0; k < c->mesh.nspecies; ++k)
+    if (lf_status st = copy_plane_in(c, 4 + k, static_cast<const char*>(rho_y) + k * n * c->elem, kind)) return st;
+  if (!on_device) LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LF_OK;
+}
+
+lf_status lf_get_partial_densities(lf_ctx* c, void* rho_y, int on_device) {
+  if (!c) return LF_ERR_ARG;
+  if (lf_status st = species_args(c, rho_y, "lf_get_partial_densities")) return st;
+  DeviceGuard g(c->cfg.device);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t n = (size_t)c->mesh.nx * c->mesh.ny;
+  for (int k = 0; k < c->mesh.nspecies; ++k)
+    if (lf_status st = copy_plane_out(c, 4 + k, static_cast<char*>(rho_y) + k * n * c->elem, kind)) return st;
+  if (!on_device) LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LF_OK;
+}
+
+lf_status lf_set_mass_fractions(lf_ctx* c, const void* y, int on_device) {
+  if (!c) return LF_ERR_ARG;
+  if (lf_status st = species_args(c, y, "lf_set_mass_fractions")) return st;
+  DeviceGuard g(c->cfg.device);
+  const size_t bytes = (size_t)c->mesh.nspecies * c->mesh.nx * c->mesh.ny * c->elem;
+  const void* src = y;
+  if (!on_device) {
+    if (lf_status st = ensure_staging(c)) return st;  // 4 planes >= LF_MAX_SPECIES planes
+    LF_CUDA(c, cudaMemcpyAsync(c->staging, y, bytes, cudaMemcpyHostToDevice, c->stream));
+    src = c->staging;
+  }
+  cudaError_t e = c->elem == 8 ? lf::launch_species_to_cons<double>(c->mesh, static_cast<const double*>(src),
+                                                                   static_cast<double*>(c->U), c->stream)
+                               : lf::launch_species_to_cons<float>(c->mesh, static_cast<const float*>(src),
+                                                                  static_cast<float*>(c->U), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "species_to_cons launch");
+  if (!on_device) LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LF_OK;
+}
+
+lf_status lf_get_mass_fractions(lf_ctx* c, void* y, int on_device) {
+  if (!c) return LF_ERR_ARG;
+  if (lf_status st = species_args(c, y, "lf_get_mass_fractions")) return st;
+  DeviceGuard g(c->cfg.device);
+  const size_t bytes = (size_t)c->mesh.nspecies * c->mesh.nx * c->mesh.ny * c->elem;
+  void* dst = y;
+  if (!on_device) {
+    if (lf_status st = ensure_staging(c)) return st;
+    dst = c->staging;
+  }
+  cudaError_t e = c->elem == 8 ? lf::launch_cons_to_species<double>(c->mesh, static_cast<const double*>(c->U),
+                                                                   static_cast<double*>(dst), c->stream)
+                               : lf::launch_cons_to_species<float>(c->mesh, static_cast<const float*>(c->U),
+                                                                  static_cast<float*>(dst), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cons_to_species launch");
+  if (!on_device) {
+    LF_CUDA(c, cudaMemcpyAsync(y, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
     LF_CUDA(c, cudaStreamSynchronize(c->stream));
   }
   return LF_OK;
@@ -502,7 +591,7 @@ lf_status lf_get_time(lf_ctx* c, double* t, int64_t* steps) {
   return LF_OK;
 }
 
-lf_status lf_conservation_sums(lf_ctx* c, double out[4]) {
+lf_status lf_conservation_sums(lf_ctx* c, double* out) {
   if (!c || !out) return LF_ERR_ARG;
   DeviceGuard g(c->cfg.device);
   cudaError_t e = c->elem == 8 ? lf::launch_sums<double>(c->mesh, static_cast<double*>(c->U), c->partials,
@@ -510,7 +599,8 @@ lf_status lf_conservation_sums(lf_ctx* c, double out[4]) {
                                : lf::launch_sums<float>(c->mesh, static_cast<float*>(c->U), c->partials,
                                                         lf::sums_blocks(), c->dsums, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "sums launch");
-  LF_CUDA(c, cudaMemcpyAsync(out, c->dsums, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LF_CUDA(c, cudaMemcpyAsync(out, c->dsums, (4 + c->mesh.nspecies) * sizeof(double), cudaMemcpyDeviceToHost,
+                             c->stream));
   LF_CUDA(c, cudaStreamSynchronize(c->stream));
   return LF_OK;
 }

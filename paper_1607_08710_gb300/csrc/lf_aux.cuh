@@ -84,40 +84,67 @@ struct KahanNeumaier {
   }
 };
 
-// Pass 1: every block sums a fixed, strided slice of the cells; the block's
-// compensated partial for field l goes to partials[(l * gridDim.x + block) * 2].
-template <typename T>
+// Pass 1: every block sums a fixed, strided slice of the cells for NS fields
+// starting at plane l0; the block's compensated partial for field l0 + l
+// goes to partials[((l0 + l) * gridDim.x + block) * 2].
+template <typename T, int NS>
 __global__ void __launch_bounds__(AUX_THREADS)
-sums_partial_kernel(const MeshDesc m, const T* __restrict__ U, double* partials) {
-  __shared__ double sh_s[4][AUX_THREADS];
-  __shared__ double sh_c[4][AUX_THREADS];
-  KahanNeumaier acc[4];
+sums_partial_kernel(const MeshDesc m, const T* __restrict__ U, int l0, double* partials) {
+  __shared__ double sh_s[NS][AUX_THREADS];
+  __shared__ double sh_c[NS][AUX_THREADS];
+  KahanNeumaier acc[NS];
   const long long n = (long long)m.nx * m.ny;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
     const long long j = k / m.nx, i = k - j * m.nx;
     const long long idx = j * m.pitch + i;
 #pragma unroll
-    for (int l = 0; l < 4; ++l) acc[l].add(double(U[l * m.plane + idx]));
+    for (int l = 0; l < NS; ++l) acc[l].add(double(U[(l0 + l) * m.plane + idx]));
   }
 #pragma unroll
-  for (int l = 0; l < 4; ++l) {
+  for (int l = 0; l < NS; ++l) {
     sh_s[l][threadIdx.x] = acc[l].s;
     sh_c[l][threadIdx.x] = acc[l].c;
   }
   __syncthreads();
-  if (threadIdx.x < 4) {
+  if (threadIdx.x < NS) {
     const int l = threadIdx.x;
     KahanNeumaier tot;
     for (int t = 0; t < AUX_THREADS; ++t) {
       tot.add(sh_s[l][t]);
       tot.add(sh_c[l][t]);
     }
-    partials[(l * gridDim.x + blockIdx.x) * 2] = tot.s;
-    partials[(l * gridDim.x + blockIdx.x) * 2 + 1] = tot.c;
+    partials[((l0 + l) * gridDim.x + blockIdx.x) * 2] = tot.s;
+    partials[((l0 + l) * gridDim.x + blockIdx.x) * 2 + 1] = tot.c;
   }
 }
 
 // Pass 2: one thread per field adds the block partials in block order.
-__global__ void sums_final_kernel(const double* partials, int nblocks, double* out);
+__global__ void sums_final_kernel(const double* partials, int nblocks, int nfields, double* out);
+
+// rho y_k = rho * y_k (y: dense planes, U: pitched state with its density set).
+template <typename T>
+__global__ void __launch_bounds__(AUX_THREADS)
+species_to_cons_kernel(const MeshDesc m, const T* y, T* U) {
+  const long long n = (long long)m.nx * m.ny;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const long long j = k / m.nx, i = k - j * m.nx;
+    const long long idx = j * m.pitch + i;
+    const T r = U[idx];
+    for (int s = 0; s < m.nspecies; ++s) U[(4 + s) * m.plane + idx] = r * y[s * n + k];
+  }
+}
+
+// y_k = (rho y_k) / rho into dense planes.
+template <typename T>
+__global__ void __launch_bounds__(AUX_THREADS)
+cons_to_species_kernel(const MeshDesc m, const T* U, T* y) {
+  const long long n = (long long)m.nx * m.ny;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const long long j = k / m.nx, i = k - j * m.nx;
+    const long long idx = j * m.pitch + i;
+    const T r = U[idx];
+    for (int s = 0; s < m.nspecies; ++s) y[s * n + k] = U[(4 + s) * m.plane + idx] / r;
+  }
+}
 
 }  // namespace lf

@@ -91,6 +91,7 @@ const char* check_problem(const lf_config* c, const lf_config* c0) {
   if (c->limiter == LF_LIMITER_SWEBY && !(c->beta >= 1.0 && c->beta <= 2.0)) return "beta out of range";
   if (c->device < 0) return "device must be >= 0";
   if (c->time_order != 0 && c->time_order != LF_TIME_HEUN) return "batched mode runs the Heun time integrator";
+  if (c->nspecies != 0) return "batched mode carries no species";
   if (c0 && (c->limiter != c0->limiter || c->bc != c0->bc || c->precision != c0->precision ||
              c->riemann != c0->riemann || c->gamma != c0->gamma || c->cfl != c0->cfl || c->beta != c0->beta ||
              c->device != c0->device))

@@ -1,6 +1,8 @@
 // Device arithmetic of the Lagrange-flux scheme (arXiv:1607.08710):
 // equation of state (eq. 1), slope limiter (eq. "sweby"), Lagrangian HLL /
-// acoustic interface solver (eqs. 13-14) and upwind Lagrange flux (eq. 12).
+// acoustic interface solver (eqs. 13-14) and upwind Lagrange flux (eq. 12),
+// with NF = 4 + nspecies fields per cell: the transported mass fractions of
+// Sec. 5 ride on the same upwind flux as (rho, rho u, rho v, rho E).
 //
 // FP64 uses IEEE division and square root throughout.  FP32 uses the
 // hardware approximate reciprocal and reciprocal square root (__fdividef,
@@ -54,15 +56,18 @@ struct Phys {
         rdx(T(m.rdx)), rdy(T(m.rdy)), riemann(m.riemann) {}
 };
 
-// Conservative (rho, rho u, rho v, rho E) -> primitive (rho, u, v, p), eq. (1).
-template <typename T>
-__device__ __forceinline__ void to_prim(const Phys<T>& P, const T U[4], T q[4]) {
+// Conservative (rho, rho u, rho v, rho E, rho y_k) -> primitive
+// (rho, u, v, p, y_k), eq. (1); y_k = (rho y_k) / rho.
+template <typename T, int NF = 4>
+__device__ __forceinline__ void to_prim(const Phys<T>& P, const T U[NF], T q[NF]) {
   T ir = Ar<T>::rcp(U[0]);
   T u = U[1] * ir, v = U[2] * ir;
   q[0] = U[0];
   q[1] = u;
   q[2] = v;
   q[3] = P.gm1 * fma_(T(-0.5), fma_(U[1], u, U[2] * v), U[3]);
+#pragma unroll
+  for (int k = 4; k < NF; ++k) q[k] = U[k] * ir;
 }
 
 // Half of the limited slope, phi(a,b)/2, so that the face states are
@@ -86,9 +91,10 @@ __device__ __forceinline__ T limiter_half(T a, T b, T beta) {
 // Eqs. (13)-(14): star pressure and normal velocity at a face from the
 // reconstructed left/right (rho, u_n, p); then eq. (12) with the upwind state
 // chosen by the sign of u*.  DIR = 0: x-face (normal velocity u), 1: y-face.
-// qL, qR are primitive (rho, u, v, p).  F receives the flux along +x / +y.
-template <typename T, int DIR>
-__device__ __forceinline__ void lagrange_flux(const Phys<T>& P, const T qL[4], const T qR[4], T F[4]) {
+// qL, qR are primitive (rho, u, v, p, y_k).  F receives the flux along +x /
+// +y; a species row is (rho_A y_k,A) u*, the mass flux's upwind side.
+template <typename T, int DIR, int NF = 4>
+__device__ __forceinline__ void lagrange_flux(const Phys<T>& P, const T qL[NF], const T qR[NF], T F[NF]) {
   const T rL = qL[0], pL = qL[3], rR = qR[0], pR = qR[3];
   const T unL = qL[1 + DIR], unR = qR[1 + DIR];
   T pstar, ustar;
@@ -125,6 +131,8 @@ __device__ __forceinline__ void lagrange_flux(const Phys<T>& P, const T qL[4], c
   F[2] = m * v;
   F[3] = (rE + pstar) * ustar;
   F[1 + DIR] += pstar;
+#pragma unroll
+  for (int k = 4; k < NF; ++k) F[k] = (r * (left ? qL[k] : qR[k])) * ustar;
 }
 
 // Local CFL speed (|u|+c)/dx + (|v|+c)/dy (1D: (|u|+c)/dx) of a cell, and its

@@ -38,7 +38,11 @@ struct MeshDesc {
   double rdx, rdy;   // 1 / dx, 1 / dy
   int vec;           // 1: pitch and plane even and every state buffer 16-byte
                      // aligned, so two adjacent cells may be moved as one vector
+  int nspecies = 0;  // transported mass fractions: planes 4 .. 3 + nspecies hold rho y_k
 };
+
+// Largest nspecies the stage kernels are built for.
+constexpr int MAX_SPECIES = 2;
 
 // Batched mode: many independent 2D meshes share one pool per state.  Each
 // problem has its own descriptor and its own Scalars (dt, t, wave-speed max).
@@ -72,6 +76,13 @@ template <typename T>
 cudaError_t launch_stage(int stage, const MeshDesc& m, const T* Uin, const T* Un, T* out,
                          Scalars* sc, cudaStream_t s);
 
+// The same for m.nspecies in 1 .. MAX_SPECIES (4 + nspecies planes per state);
+// built in their own translation units.
+cudaError_t launch_stage_species(int stage, const MeshDesc& m, const float* Uin, const float* Un, float* out,
+                                 Scalars* sc, cudaStream_t s);
+cudaError_t launch_stage_species(int stage, const MeshDesc& m, const double* Uin, const double* Un, double* out,
+                                 Scalars* sc, cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_wave_speed(const MeshDesc& m, const T* U, Scalars* sc, cudaStream_t s);
 
@@ -82,6 +93,15 @@ cudaError_t launch_prim_to_cons(const MeshDesc& m, const T* rho, const T* u, con
 template <typename T>
 cudaError_t launch_cons_to_prim(const MeshDesc& m, const T* U, T* rho, T* u, T* v, T* p, cudaStream_t s);
 
+// Species planes of U from dense mass-fraction planes y (nspecies planes of
+// nx*ny): rho y_k = rho * y_k with the density already in U; and back.
+template <typename T>
+cudaError_t launch_species_to_cons(const MeshDesc& m, const T* y, T* U, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cons_to_species(const MeshDesc& m, const T* U, T* y, cudaStream_t s);
+
+// Compensated sums of the 4 + m.nspecies conserved fields (partials: blocks x
+// fields x 2 doubles; out: 4 + m.nspecies doubles).
 template <typename T>
 cudaError_t launch_sums(const MeshDesc& m, const T* U, double* partials, int nblocks, double* out,
                         cudaStream_t s);

@@ -17,7 +17,8 @@ inline int aux_blocks(long long n) {
 template <typename T>
 cudaError_t launch_stage(int stage, const MeshDesc& m, const T* Uin, const T* Un, T* out, Scalars* sc,
                          cudaStream_t s) {
-  return launch_stage_impl<T>(stage, m, Uin, Un, out, sc, s);
+  if (m.nspecies > 0) return launch_stage_species(stage, m, Uin, Un, out, sc, s);
+  return launch_stage_nf<T, 4>(stage, m, Uin, Un, out, sc, s);
 }
 
 template <typename T>
@@ -53,10 +54,25 @@ cudaError_t launch_cons_to_prim(const MeshDesc& m, const T* U, T* rho, T* u, T* 
 }
 
 template <typename T>
+cudaError_t launch_species_to_cons(const MeshDesc& m, const T* y, T* U, cudaStream_t s) {
+  species_to_cons_kernel<T><<<aux_blocks((long long)m.nx * m.ny), AUX_THREADS, 0, s>>>(m, y, U);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cons_to_species(const MeshDesc& m, const T* U, T* y, cudaStream_t s) {
+  cons_to_species_kernel<T><<<aux_blocks((long long)m.nx * m.ny), AUX_THREADS, 0, s>>>(m, U, y);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_sums(const MeshDesc& m, const T* U, double* partials, int nblocks, double* out,
                         cudaStream_t s) {
-  sums_partial_kernel<T><<<nblocks, AUX_THREADS, 0, s>>>(m, U, partials);
-  sums_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, out);
+  sums_partial_kernel<T, 4><<<nblocks, AUX_THREADS, 0, s>>>(m, U, 0, partials);
+  if (m.nspecies == 1) sums_partial_kernel<T, 1><<<nblocks, AUX_THREADS, 0, s>>>(m, U, 4, partials);
+  else if (m.nspecies == 2) sums_partial_kernel<T, 2><<<nblocks, AUX_THREADS, 0, s>>>(m, U, 4, partials);
+  static_assert(MAX_SPECIES == 2, "species sums cover nspecies <= 2");
+  sums_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, 4 + m.nspecies, out);
   return cudaGetLastError();
 }
 
@@ -112,6 +128,8 @@ cudaError_t launch_grad_prim(const MeshDesc& m, const T* U0, const T* lam, T* gq
                                               long long, T*, cudaStream_t);                            \
   template cudaError_t launch_cons_to_prim<T>(const MeshDesc&, const T*, T*, T*, T*, T*, cudaStream_t); \
   template cudaError_t launch_sums<T>(const MeshDesc&, const T*, double*, int, double*, cudaStream_t);      \
+  template cudaError_t launch_species_to_cons<T>(const MeshDesc&, const T*, T*, cudaStream_t);           \
+  template cudaError_t launch_cons_to_species<T>(const MeshDesc&, const T*, T*, cudaStream_t);           \
   template cudaError_t launch_face_vjp<T>(const MeshDesc&, int, const T*, const T*, T*, cudaStream_t);        \
   template cudaError_t launch_cell_vjp<T>(const MeshDesc&, const T*, const T*, const T*, const T*, double,    \
                                           const T*, double, double, T*, cudaStream_t);                      \

@@ -73,6 +73,7 @@ const char* check_config(const lf_config* c) {
   if (!(c->gamma > 1.0 && c->gamma <= 3.0) || !(c->cfl > 0.0 && c->cfl <= 1.0)) return "gamma or cfl out of range";
   if (c->limiter == LF_LIMITER_SWEBY && !(c->beta >= 1.0 && c->beta <= 2.0)) return "beta out of range";
   if (c->time_order != 0 && c->time_order != LF_TIME_HEUN) return "only the Heun time integrator";
+  if (c->nspecies != 0) return "no species";
   return nullptr;
 }
 

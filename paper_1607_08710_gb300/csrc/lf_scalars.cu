@@ -73,8 +73,8 @@ __global__ void reset_scalars_kernel(Scalars* sc, double cfl) {
 
 __global__ void set_t_end_kernel(Scalars* sc, double t_end) { sc->t_end = t_end; }
 
-__global__ void sums_final_kernel(const double* partials, int nblocks, double* out) {
-  if (threadIdx.x < 4) {
+__global__ void sums_final_kernel(const double* partials, int nblocks, int nfields, double* out) {
+  if (threadIdx.x < nfields) {
     const int l = threadIdx.x;
     KahanNeumaier tot;
     for (int b = 0; b < nblocks; ++b) {

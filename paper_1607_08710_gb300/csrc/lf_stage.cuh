@@ -2,7 +2,9 @@
 // per cell, primitive conversion (eq. 1), limited MUSCL slopes in x and y
 // (eq. "sweby"), face states, the acoustic interface solve (eqs. 13-14), the
 // upwind Lagrange flux (eq. 12) and the conservative update -- one kernel per
-// stage, no face quantity ever written to memory.
+// stage, no face quantity ever written to memory.  A cell carries NF = 4 +
+// nspecies fields: the transported mass fractions of Sec. 5 are reconstructed
+// and upwinded with the gas state, so they add planes, not passes.
 //
 // Work decomposition.  A warp owns a strip of 32*CPL consecutive columns,
 // CPL cells per lane.  The two columns at each end are the halo the 5-point
@@ -126,12 +128,12 @@ __device__ __forceinline__ LaneCols<CPL> lane_cols(int i0, int lane, int nx, int
 }
 
 // Conservative values of this lane's CPL cells in row `off` (= mapped row * pitch).
-template <typename T, int CPL>
-__device__ __forceinline__ void load_row(const T* const __restrict__ P[4], const LaneCols<CPL>& L, int off,
-                                         T U[CPL][4]) {
+template <typename T, int CPL, int NF>
+__device__ __forceinline__ void load_row(const T* const __restrict__ P[NF], const LaneCols<CPL>& L, int off,
+                                         T U[CPL][NF]) {
   if (L.vec_ok) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < NF; ++k) {
       T v[CPL];
       VecLoad<T, CPL>::load(P[k] + off + L.c0, v);
 #pragma unroll
@@ -139,7 +141,7 @@ __device__ __forceinline__ void load_row(const T* const __restrict__ P[4], const
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < NF; ++k)
 #pragma unroll
       for (int j = 0; j < CPL; ++j) U[j][k] = __ldg(P[k] + off + L.ic[j]);
   }
@@ -148,12 +150,12 @@ __device__ __forceinline__ void load_row(const T* const __restrict__ P[4], const
 // Fluxes through the x-faces of this lane's cells, from the primitive states
 // q of the lane's CPL columns in the current row.  Fl[j] / Fr[j]: left and
 // right face of cell j (valid for output cells).
-template <typename T, int LIM, int CPL>
-__device__ __forceinline__ void x_fluxes(const Phys<T>& P, const T q[CPL][4], T Fl[CPL][4], T Fr[CPL][4]) {
+template <typename T, int LIM, int CPL, int NF>
+__device__ __forceinline__ void x_fluxes(const Phys<T>& P, const T q[CPL][NF], T Fl[CPL][NF], T Fr[CPL][NF]) {
   constexpr unsigned FULL = 0xffffffffu;
-  T qL[CPL][4], qR[CPL][4];  // qL[j]: left state of face j+1/2; qR[j]: right state of face j-1/2
+  T qL[CPL][NF], qR[CPL][NF];  // qL[j]: left state of face j+1/2; qR[j]: right state of face j-1/2
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < NF; ++k) {
     const T left = __shfl_up_sync(FULL, q[CPL - 1][k], 1);  // column c0-1
     const T right = __shfl_down_sync(FULL, q[0][k], 1);     // column c0+CPL
     T dminus = q[0][k] - left;
@@ -169,16 +171,16 @@ __device__ __forceinline__ void x_fluxes(const Phys<T>& P, const T q[CPL][4], T 
   // internal faces j+1/2 for j < CPL-1, then the face shared with the next lane
 #pragma unroll
   for (int j = 0; j + 1 < CPL; ++j) {
-    lagrange_flux<T, 0>(P, qL[j], qR[j + 1], Fr[j]);
+    lagrange_flux<T, 0, NF>(P, qL[j], qR[j + 1], Fr[j]);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) Fl[j + 1][k] = Fr[j][k];
+    for (int k = 0; k < NF; ++k) Fl[j + 1][k] = Fr[j][k];
   }
-  T qRnext[4];
+  T qRnext[NF];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) qRnext[k] = __shfl_down_sync(FULL, qR[0][k], 1);
-  lagrange_flux<T, 0>(P, qL[CPL - 1], qRnext, Fr[CPL - 1]);
+  for (int k = 0; k < NF; ++k) qRnext[k] = __shfl_down_sync(FULL, qR[0][k], 1);
+  lagrange_flux<T, 0, NF>(P, qL[CPL - 1], qRnext, Fr[CPL - 1]);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) Fl[0][k] = __shfl_up_sync(FULL, Fr[CPL - 1][k], 1);
+  for (int k = 0; k < NF; ++k) Fl[0][k] = __shfl_up_sync(FULL, Fr[CPL - 1][k], 1);
 }
 
 // Warp-level max and any(), then one atomic per warp.
@@ -224,17 +226,17 @@ __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;
 // laid out [field][lane][cell].
 constexpr int RING_IN = 5, RING_UN = 3, AHEAD_IN = 4, AHEAD_UN = 2;
 
-template <typename T, int CPL> struct Ring {
-  static constexpr int ROW = 4 * 32 * CPL;  // elements per buffer
+template <typename T, int CPL, int NF> struct Ring {
+  static constexpr int ROW = NF * 32 * CPL;  // elements per buffer
   static __host__ __device__ constexpr int buffers(int stage) { return RING_IN + (stage ? RING_UN : 0); }
   static __host__ __device__ constexpr size_t warp_bytes(int stage) { return (size_t)buffers(stage) * ROW * sizeof(T); }
 };
 
 // Copies this lane's cells of (mapped) row offset `off` into buffer `buf`.
-template <typename T, int CPL>
-__device__ __forceinline__ void issue_row(T* buf, const T* const P[4], const LaneCols<CPL>& L, int off, int lane) {
+template <typename T, int CPL, int NF>
+__device__ __forceinline__ void issue_row(T* buf, const T* const P[NF], const LaneCols<CPL>& L, int off, int lane) {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < NF; ++k) {
     T* dst = buf + (k * 32 + lane) * CPL;
     const T* src = P[k] + off;
     if (L.vec_ok) {
@@ -247,11 +249,11 @@ __device__ __forceinline__ void issue_row(T* buf, const T* const P[4], const Lan
 }
 
 // Same for the output cells only (row offset `off` inside the mesh).
-template <typename T, int CPL>
-__device__ __forceinline__ void issue_out_cells(T* buf, const T* const P[4], const LaneCols<CPL>& L, int off,
+template <typename T, int CPL, int NF>
+__device__ __forceinline__ void issue_out_cells(T* buf, const T* const P[NF], const LaneCols<CPL>& L, int off,
                                                 int lane) {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < NF; ++k) {
     T* dst = buf + (k * 32 + lane) * CPL;
     const T* src = P[k] + off + L.c0;
     if (L.vec_ok) {
@@ -264,10 +266,10 @@ __device__ __forceinline__ void issue_out_cells(T* buf, const T* const P[4], con
   }
 }
 
-template <typename T, int CPL>
-__device__ __forceinline__ void read_row(const T* buf, int lane, T V[CPL][4]) {
+template <typename T, int CPL, int NF>
+__device__ __forceinline__ void read_row(const T* buf, int lane, T V[CPL][NF]) {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < NF; ++k) {
     T v[CPL];
     VecLoad<T, CPL>::load_plain(buf + (k * 32 + lane) * CPL, v);
 #pragma unroll
@@ -289,16 +291,16 @@ template <> struct StageCoef<2> { static constexpr double alpha = 0.75, beta = 0
 template <> struct StageCoef<3> { static constexpr double alpha = 1.0 / 3.0, beta = 2.0 / 3.0; static constexpr bool speed = true; };
 
 // State of the y-march: three register slots indexed by row mod 3.
-template <typename T, int CPL> struct March {
-  T q[3][CPL][4];  // primitives of rows r, r+1, r+2
-  T s[3][CPL][4];  // half y-slopes (limiter_half)
-  T G[3][CPL][4];  // G[slot(r)] = flux through face r-1/2
+template <typename T, int CPL, int NF> struct March {
+  T q[3][CPL][NF];  // primitives of rows r, r+1, r+2
+  T s[3][CPL][NF];  // half y-slopes (limiter_half)
+  T G[3][CPL][NF];  // G[slot(r)] = flux through face r-1/2
 };
 
-template <typename T, int STAGE, int CPL> struct StageArgs {
-  const T* P[4];  // Uin planes (read with halo)
-  const T* N[4];  // U^n planes (corrector, read at the cell)
-  T* O[4];        // output planes
+template <typename T, int STAGE, int CPL, int NF> struct StageArgs {
+  const T* P[NF];  // Uin planes (read with halo)
+  const T* N[NF];  // U^n planes (corrector, read at the cell)
+  T* O[NF];        // output planes
   T* ring_in;     // this warp's input ring
   T* ring_un;     // this warp's U^n ring (corrector)
   int j0;         // first row of the tile
@@ -313,56 +315,57 @@ __device__ __forceinline__ int ring_in_plus(int si, int k) {
   return t >= RING_IN ? t - RING_IN : t;
 }
 
-template <typename T, int LIM, int STAGE, int CPL, int S>
-__device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, const StageArgs<T, STAGE, CPL>& A,
-                                          const LaneCols<CPL>& L, March<T, CPL>& M, int lane, int r, int si,
-                                          int jend, T cx, T cy, T& smax, bool& bad) {
+template <typename T, int LIM, int STAGE, int CPL, int NF, int S>
+__device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m,
+                                          const StageArgs<T, STAGE, CPL, NF>& A, const LaneCols<CPL>& L,
+                                          March<T, CPL, NF>& M, int lane, int r, int si, int jend, T cx, T cy,
+                                          T& smax, bool& bad) {
   constexpr int S1 = (S + 1) % 3, S2 = (S + 2) % 3;
-  constexpr int ROW = Ring<T, CPL>::ROW;
+  constexpr int ROW = Ring<T, CPL, NF>::ROW;
   static_assert(RING_UN == 3, "the U^n ring is indexed by the register slot");
   // the group issued two rows ago (input row r+2, U^n row r) has landed
   cp_wait<1>();
   {
-    T Ut[CPL][4];
-    read_row<T, CPL>(A.ring_in + ring_in_plus(si, 2) * ROW, lane, Ut);
+    T Ut[CPL][NF];
+    read_row<T, CPL, NF>(A.ring_in + ring_in_plus(si, 2) * ROW, lane, Ut);
 #pragma unroll
-    for (int j = 0; j < CPL; ++j) to_prim(P, Ut[j], M.q[S2][j]);
+    for (int j = 0; j < CPL; ++j) to_prim<T, NF>(P, Ut[j], M.q[S2][j]);
   }
   // Rows r+4 (input) and r+2 (U^n) are issued on every row, also near the
   // end of the tile where they are not needed: the row index stays valid
   // (boundary-mapped, or clamped to the last row) and the target buffers
   // (rows r-1) are no longer read, so the branch-free row body costs two idle
   // copies per tile.  strip_tile drains them before returning.
-  issue_row<T, CPL>(A.ring_in + ring_in_plus(si, AHEAD_IN) * ROW, A.P, L, map_row(r + AHEAD_IN, m.ny, m.bc) * m.pitch,
-                    lane);
+  issue_row<T, CPL, NF>(A.ring_in + ring_in_plus(si, AHEAD_IN) * ROW, A.P, L,
+                        map_row(r + AHEAD_IN, m.ny, m.bc) * m.pitch, lane);
   if (STAGE >= 1 && L.any_out)  // U^n row r+2 lives in register slot S2's ring buffer
-    issue_out_cells<T, CPL>(A.ring_un + S2 * ROW, A.N, L, min(r + AHEAD_UN, m.ny - 1) * m.pitch, lane);
+    issue_out_cells<T, CPL, NF>(A.ring_un + S2 * ROW, A.N, L, min(r + AHEAD_UN, m.ny - 1) * m.pitch, lane);
   cp_commit();
   // y-slopes of row r+1 and the flux through face r+1/2
 #pragma unroll
   for (int j = 0; j < CPL; ++j) {
-    T Lq[4], Rq[4];
+    T Lq[NF], Rq[NF];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < NF; ++k) {
       M.s[S1][j][k] = limiter_half<T, LIM>(M.q[S1][j][k] - M.q[S][j][k], M.q[S2][j][k] - M.q[S1][j][k], P.beta);
       Lq[k] = M.q[S][j][k] + M.s[S][j][k];
       Rq[k] = M.q[S1][j][k] - M.s[S1][j][k];
     }
-    lagrange_flux<T, 1>(P, Lq, Rq, M.G[S1][j]);
+    lagrange_flux<T, 1, NF>(P, Lq, Rq, M.G[S1][j]);
   }
   // x-faces of row r
-  T Fl[CPL][4], Fr[CPL][4];
-  x_fluxes<T, LIM, CPL>(P, M.q[S], Fl, Fr);
+  T Fl[CPL][NF], Fr[CPL][NF];
+  x_fluxes<T, LIM, CPL, NF>(P, M.q[S], Fl, Fr);
   // update the output cells of row r (computed on every lane; only output
   // cells are stored and enter the wave-speed maximum)
-  T U[CPL][4], Un[CPL][4];
-  read_row<T, CPL>(A.ring_in + si * ROW, lane, U);
-  if (STAGE >= 1) read_row<T, CPL>(A.ring_un + S * ROW, lane, Un);
-  T W[CPL][4];
+  T U[CPL][NF], Un[CPL][NF];
+  read_row<T, CPL, NF>(A.ring_in + si * ROW, lane, U);
+  if (STAGE >= 1) read_row<T, CPL, NF>(A.ring_un + S * ROW, lane, Un);
+  T W[CPL][NF];
 #pragma unroll
   for (int j = 0; j < CPL; ++j)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < NF; ++k) {
       const T base = STAGE == 0 ? U[j][k]
                     : STAGE == 1 ? T(0.5) * (Un[j][k] + U[j][k])
                                  : fma_(T(StageCoef<STAGE>::alpha), Un[j][k], T(StageCoef<STAGE>::beta) * U[j][k]);
@@ -371,7 +374,7 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, c
   const int off = r * m.pitch;
   if (L.vec_ok && L.any_out) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < NF; ++k) {
       T v[CPL];
 #pragma unroll
       for (int j = 0; j < CPL; ++j) v[j] = W[j][k];
@@ -382,7 +385,7 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, c
     for (int j = 0; j < CPL; ++j)
       if (L.out[j])
 #pragma unroll
-        for (int k = 0; k < 4; ++k) A.O[k][off + L.c0 + j] = W[j][k];
+        for (int k = 0; k < NF; ++k) A.O[k][off + L.c0 + j] = W[j][k];
   }
   if (StageCoef<STAGE>::speed) {
 #pragma unroll
@@ -399,15 +402,15 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m, c
 // [j0, jend): the whole y-march, from the prologue to the last row.  The
 // warp's rings start empty and are left with no copy in flight.
 // STAGE 0: out = Uin - dt L(Uin).  STAGE 1: out = (Un + Uin)/2 - dt/2 L(Uin).
-template <typename T, int LIM, int STAGE, int CPL>
+template <typename T, int LIM, int STAGE, int CPL, int NF>
 __device__ __forceinline__ void strip_tile(const Phys<T>& P, const MeshDesc& m, const T* Uin, const T* Un, T* out,
                                            int i0, int j0, int jend, T cx, T cy, T* ring_in, int lane, T& smax,
                                            bool& bad) {
   const LaneCols<CPL> L = lane_cols<CPL>(i0, lane, m.nx, m.bc, m.vec);
-  constexpr int ROW = Ring<T, CPL>::ROW;
-  StageArgs<T, STAGE, CPL> A;
+  constexpr int ROW = Ring<T, CPL, NF>::ROW;
+  StageArgs<T, STAGE, CPL, NF> A;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < NF; ++k) {
     A.P[k] = Uin + k * m.plane;
     A.N[k] = Un + k * m.plane;
     A.O[k] = out + k * m.plane;
@@ -422,55 +425,55 @@ __device__ __forceinline__ void strip_tile(const Phys<T>& P, const MeshDesc& m, 
   // and the flux through face j0-1/2 (slot 0).  Group 2 (input row j0+3, U^n
   // row j0+1) reuses row j0-2's buffer, so it is issued after that row is read.
   for (int row = j0 - 2; row <= j0 + 1; ++row)
-    issue_row<T, CPL>(A.ring_in + ring_slot(row, j0, RING_IN) * ROW, A.P, L, map_row(row, m.ny, m.bc) * m.pitch,
+    issue_row<T, CPL, NF>(A.ring_in + ring_slot(row, j0, RING_IN) * ROW, A.P, L, map_row(row, m.ny, m.bc) * m.pitch,
                       lane);
   cp_commit();
-  issue_row<T, CPL>(A.ring_in + ring_slot(j0 + 2, j0, RING_IN) * ROW, A.P, L, map_row(j0 + 2, m.ny, m.bc) * m.pitch,
-                    lane);
-  if (STAGE >= 1 && L.any_out) issue_out_cells<T, CPL>(A.ring_un + 0 * ROW, A.N, L, j0 * m.pitch, lane);
+  issue_row<T, CPL, NF>(A.ring_in + ring_slot(j0 + 2, j0, RING_IN) * ROW, A.P, L,
+                        map_row(j0 + 2, m.ny, m.bc) * m.pitch, lane);
+  if (STAGE >= 1 && L.any_out) issue_out_cells<T, CPL, NF>(A.ring_un + 0 * ROW, A.N, L, j0 * m.pitch, lane);
   cp_commit();
   cp_wait<1>();
-  March<T, CPL> M;
+  March<T, CPL, NF> M;
   {
-    T Ut[CPL][4];
+    T Ut[CPL][NF];
     const int slot_of[4] = {1, 2, 0, 1};  // rows j0-2, j0-1, j0, j0+1 -> register slots
-    T qm2[CPL][4];
+    T qm2[CPL][NF];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      read_row<T, CPL>(A.ring_in + ring_slot(j0 - 2 + t, j0, RING_IN) * ROW, lane, Ut);
+      read_row<T, CPL, NF>(A.ring_in + ring_slot(j0 - 2 + t, j0, RING_IN) * ROW, lane, Ut);
 #pragma unroll
-      for (int j = 0; j < CPL; ++j) to_prim(P, Ut[j], t == 0 ? qm2[j] : M.q[slot_of[t]][j]);
+      for (int j = 0; j < CPL; ++j) to_prim<T, NF>(P, Ut[j], t == 0 ? qm2[j] : M.q[slot_of[t]][j]);
     }
 #pragma unroll
     for (int j = 0; j < CPL; ++j) {
-      T Lq[4], Rq[4];
+      T Lq[NF], Rq[NF];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < NF; ++k) {
         M.s[2][j][k] = limiter_half<T, LIM>(M.q[2][j][k] - qm2[j][k], M.q[0][j][k] - M.q[2][j][k], P.beta);
         M.s[0][j][k] = limiter_half<T, LIM>(M.q[0][j][k] - M.q[2][j][k], M.q[1][j][k] - M.q[0][j][k], P.beta);
         Lq[k] = M.q[2][j][k] + M.s[2][j][k];
         Rq[k] = M.q[0][j][k] - M.s[0][j][k];
       }
-      lagrange_flux<T, 1>(P, Lq, Rq, M.G[0][j]);
+      lagrange_flux<T, 1, NF>(P, Lq, Rq, M.G[0][j]);
     }
   }
   if (j0 + 1 < jend) {
-    issue_row<T, CPL>(A.ring_in + ring_slot(j0 + 3, j0, RING_IN) * ROW, A.P, L,
-                      map_row(j0 + 3, m.ny, m.bc) * m.pitch, lane);
+    issue_row<T, CPL, NF>(A.ring_in + ring_slot(j0 + 3, j0, RING_IN) * ROW, A.P, L,
+                          map_row(j0 + 3, m.ny, m.bc) * m.pitch, lane);
     if (STAGE >= 1 && L.any_out)
-      issue_out_cells<T, CPL>(A.ring_un + 1 * ROW, A.N, L, (j0 + 1) * m.pitch, lane);
+      issue_out_cells<T, CPL, NF>(A.ring_un + 1 * ROW, A.N, L, (j0 + 1) * m.pitch, lane);
   }
   cp_commit();
 
   // si: input-ring slot of row r (row j0 is in slot 0)
   for (int r = j0, si = 0;;) {
-    march_row<T, LIM, STAGE, CPL, 0>(P, m, A, L, M, lane, r, si, jend, cx, cy, smax, bad);
+    march_row<T, LIM, STAGE, CPL, NF, 0>(P, m, A, L, M, lane, r, si, jend, cx, cy, smax, bad);
     if (++r >= jend) break;
     si = ring_in_plus(si, 1);
-    march_row<T, LIM, STAGE, CPL, 1>(P, m, A, L, M, lane, r, si, jend, cx, cy, smax, bad);
+    march_row<T, LIM, STAGE, CPL, NF, 1>(P, m, A, L, M, lane, r, si, jend, cx, cy, smax, bad);
     if (++r >= jend) break;
     si = ring_in_plus(si, 1);
-    march_row<T, LIM, STAGE, CPL, 2>(P, m, A, L, M, lane, r, si, jend, cx, cy, smax, bad);
+    march_row<T, LIM, STAGE, CPL, NF, 2>(P, m, A, L, M, lane, r, si, jend, cx, cy, smax, bad);
     if (++r >= jend) break;
     si = ring_in_plus(si, 1);
   }
@@ -478,16 +481,26 @@ __device__ __forceinline__ void strip_tile(const Phys<T>& P, const MeshDesc& m, 
 }
 
 // One mesh: a 2D grid of (strips / STAGE_WARPS) x (row tiles) CTAs.
-// Dynamic shared memory: STAGE_WARPS * Ring<T,CPL>::warp_bytes(STAGE).
+// Dynamic shared memory: STAGE_WARPS * Ring<T,CPL,NF>::warp_bytes(STAGE).
 // Resident CTAs per SM requested from the register allocator: FP32 stages are
 // issue-bound and gain from more warps (predictor 18 CTAs -> 92 registers,
-// corrector 16 -> 114, no spills); FP64 is bound by its arithmetic pipe and
-// keeps the registers it wants.
-template <typename T, int STAGE> struct MinBlocks { static constexpr int value = STAGE == 0 ? LF_MIN_BLOCKS0 : LF_MIN_BLOCKS1; };
-template <int STAGE> struct MinBlocks<double, STAGE> { static constexpr int value = 1; };
+// corrector 16 -> 114, no spills); with species the march carries more
+// fields and gets more registers per thread; FP64 is bound by its arithmetic
+// pipe and keeps the registers it wants.
+#ifndef LF_MIN_BLOCKS_SPECIES0
+#define LF_MIN_BLOCKS_SPECIES0 12
+#endif
+#ifndef LF_MIN_BLOCKS_SPECIES1
+#define LF_MIN_BLOCKS_SPECIES1 10
+#endif
+template <typename T, int STAGE, int NF> struct MinBlocks {
+  static constexpr int value = NF == 4 ? (STAGE == 0 ? LF_MIN_BLOCKS0 : LF_MIN_BLOCKS1)
+                                       : (STAGE == 0 ? LF_MIN_BLOCKS_SPECIES0 : LF_MIN_BLOCKS_SPECIES1);
+};
+template <int STAGE, int NF> struct MinBlocks<double, STAGE, NF> { static constexpr int value = 1; };
 
-template <typename T, int LIM, int STAGE, int CPL, int TY>
-__global__ void __launch_bounds__(STAGE_WARPS * 32, (MinBlocks<T, STAGE>::value))
+template <typename T, int LIM, int STAGE, int CPL, int TY, int NF>
+__global__ void __launch_bounds__(STAGE_WARPS * 32, (MinBlocks<T, STAGE, NF>::value))
 stage2d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out, Scalars* sc) {
   extern __shared__ __align__(16) unsigned char lf_stage_smem[];
   const double dtd = sc->dt;
@@ -501,16 +514,17 @@ stage2d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
   const int jend = min(j0 + TY, m.ny);
   const double hs = StageCoef<STAGE>::beta;
   const T cx = T(hs * dtd * m.rdx), cy = T(hs * dtd * m.rdy);
-  T* ring = reinterpret_cast<T*>(lf_stage_smem + warp * Ring<T, CPL>::warp_bytes(STAGE));
+  T* ring = reinterpret_cast<T*>(lf_stage_smem + warp * Ring<T, CPL, NF>::warp_bytes(STAGE));
   T smax = T(0);
   bool bad = false;
-  strip_tile<T, LIM, STAGE, CPL>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring, lane, smax, bad);
+  strip_tile<T, LIM, STAGE, CPL, NF>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring, lane, smax, bad);
   if (StageCoef<STAGE>::speed) publish_speed(sc, wpar, smax, bad);
 }
 
 // Many meshes: a persistent grid whose warps pull work units (problem, strip,
 // row tile) from an atomic counter until the list is exhausted.  Each problem
 // uses its own dt, and its corrector units feed its own wave-speed maximum.
+// (Gas dynamics only: NF = 4.)
 #ifndef LF_BATCH_MIN_BLOCKS
 #define LF_BATCH_MIN_BLOCKS (16 / LF_STAGE_WARPS)
 #endif
@@ -523,7 +537,7 @@ batch_stage_kernel(const BatchDesc b, const T* Uin, const T* Un, T* out, Scalars
   extern __shared__ __align__(16) unsigned char lf_stage_smem[];
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T* ring = reinterpret_cast<T*>(lf_stage_smem + warp * Ring<T, CPL>::warp_bytes(STAGE));
+  T* ring = reinterpret_cast<T*>(lf_stage_smem + warp * Ring<T, CPL, 4>::warp_bytes(STAGE));
   for (;;) {
     int u = 0;
     if (lane == 0) u = atomicAdd(counter, 1);
@@ -546,8 +560,8 @@ batch_stage_kernel(const BatchDesc b, const T* Uin, const T* Un, T* out, Scalars
     const T cx = T(hs * dtd * m.rdx), cy = T(hs * dtd * m.rdy);
     T smax = T(0);
     bool bad = false;
-    strip_tile<T, LIM, STAGE, CPL>(P, m, Uin + pd.off, Un + pd.off, out + pd.off, un.i0, un.j0, un.jend, cx, cy,
-                                   ring, lane, smax, bad);
+    strip_tile<T, LIM, STAGE, CPL, 4>(P, m, Uin + pd.off, Un + pd.off, out + pd.off, un.i0, un.j0, un.jend, cx, cy,
+                                      ring, lane, smax, bad);
     if (StageCoef<STAGE>::speed) publish_speed(scp, scp->parity ^ 1, smax, bad);
   }
 }
@@ -556,7 +570,7 @@ template <typename T, int LIM>
 cudaError_t launch_batch_stage_lim(int stage, const BatchDesc& b, const T* Uin, const T* Un, T* out, Scalars* sc,
                                    int* counter, cudaStream_t s) {
   constexpr int CPL = StageShape<T>::CPL;
-  const size_t smem = STAGE_WARPS * Ring<T, CPL>::warp_bytes(stage);
+  const size_t smem = STAGE_WARPS * Ring<T, CPL, 4>::warp_bytes(stage);
   if (stage == 0) batch_stage_kernel<T, LIM, 0, CPL><<<b.grid, STAGE_WARPS * 32, smem, s>>>(b, Uin, Un, out, sc, counter);
   else batch_stage_kernel<T, LIM, 1, CPL><<<b.grid, STAGE_WARPS * 32, smem, s>>>(b, Uin, Un, out, sc, counter);
   return cudaGetLastError();
@@ -565,7 +579,7 @@ cudaError_t launch_batch_stage_lim(int stage, const BatchDesc& b, const T* Uin, 
 template <typename T, int LIM>
 int batch_blocks_lim(int stage) {
   constexpr int CPL = StageShape<T>::CPL;
-  const size_t smem = STAGE_WARPS * Ring<T, CPL>::warp_bytes(stage);
+  const size_t smem = STAGE_WARPS * Ring<T, CPL, 4>::warp_bytes(stage);
   int nb = 0;
   cudaError_t e = stage == 0
       ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_stage_kernel<T, LIM, 0, CPL>, STAGE_WARPS * 32, smem)
@@ -574,7 +588,7 @@ int batch_blocks_lim(int stage) {
 }
 
 // 1D: one row, no y-terms.
-template <typename T, int LIM, int STAGE, int CPL>
+template <typename T, int LIM, int STAGE, int CPL, int NF>
 __global__ void __launch_bounds__(STAGE_WARPS * 32)
 stage1d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out, Scalars* sc) {
   const double dtd = sc->dt;
@@ -586,28 +600,30 @@ stage1d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
   if (i0 >= m.nx) return;
   const LaneCols<CPL> L = lane_cols<CPL>(i0, lane, m.nx, m.bc, m.vec);
   const T cx = T(StageCoef<STAGE>::beta * dtd * m.rdx);
-  const T* Pp[4] = {Uin, Uin + m.plane, Uin + 2 * m.plane, Uin + 3 * m.plane};
-  T U[CPL][4], q[CPL][4], Fl[CPL][4], Fr[CPL][4];
-  load_row<T, CPL>(Pp, L, 0, U);
+  const T* Pp[NF];
 #pragma unroll
-  for (int j = 0; j < CPL; ++j) to_prim(P, U[j], q[j]);
-  x_fluxes<T, LIM, CPL>(P, q, Fl, Fr);
+  for (int k = 0; k < NF; ++k) Pp[k] = Uin + k * m.plane;
+  T U[CPL][NF], q[CPL][NF], Fl[CPL][NF], Fr[CPL][NF];
+  load_row<T, CPL, NF>(Pp, L, 0, U);
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) to_prim<T, NF>(P, U[j], q[j]);
+  x_fluxes<T, LIM, CPL, NF>(P, q, Fl, Fr);
   T smax = T(0);
   bool bad = false;
 #pragma unroll
   for (int j = 0; j < CPL; ++j) {
     if (!L.out[j]) continue;
     const int c = L.c0 + j;
-    T W[4];
+    T W[NF];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < NF; ++k) {
       const T base = STAGE == 0 ? U[j][k]
                     : STAGE == 1 ? T(0.5) * (Un[k * m.plane + c] + U[j][k])
                                  : fma_(T(StageCoef<STAGE>::alpha), Un[k * m.plane + c], T(StageCoef<STAGE>::beta) * U[j][k]);
       W[k] = fma_(-cx, Fr[j][k] - Fl[j][k], base);
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) out[k * m.plane + c] = W[k];
+    for (int k = 0; k < NF; ++k) out[k * m.plane + c] = W[k];
     if (StageCoef<STAGE>::speed) {
       bool ok;
       smax = fmax(smax, cell_speed<T, 1>(P, W, ok));
@@ -617,7 +633,7 @@ stage1d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
   if (StageCoef<STAGE>::speed) publish_speed(sc, wpar, smax, bad);
 }
 
-template <typename T, int LIM>
+template <typename T, int LIM, int NF>
 cudaError_t launch_stage_lim(int stage, const MeshDesc& m, const T* Uin, const T* Un, T* out, Scalars* sc,
                              cudaStream_t s) {
   constexpr int CPL = StageShape<T>::CPL, TY = StageShape<T>::TY;
@@ -626,19 +642,19 @@ cudaError_t launch_stage_lim(int stage, const MeshDesc& m, const T* Uin, const T
   if (m.dim == 1) {
     dim3 grid((strips + STAGE_WARPS - 1) / STAGE_WARPS);
     switch (stage) {
-      case 0: stage1d_kernel<T, LIM, 0, CPL><<<grid, block, 0, s>>>(m, Uin, Un, out, sc); break;
-      case 1: stage1d_kernel<T, LIM, 1, CPL><<<grid, block, 0, s>>>(m, Uin, Un, out, sc); break;
-      case 2: stage1d_kernel<T, LIM, 2, CPL><<<grid, block, 0, s>>>(m, Uin, Un, out, sc); break;
-      default: stage1d_kernel<T, LIM, 3, CPL><<<grid, block, 0, s>>>(m, Uin, Un, out, sc);
+      case 0: stage1d_kernel<T, LIM, 0, CPL, NF><<<grid, block, 0, s>>>(m, Uin, Un, out, sc); break;
+      case 1: stage1d_kernel<T, LIM, 1, CPL, NF><<<grid, block, 0, s>>>(m, Uin, Un, out, sc); break;
+      case 2: stage1d_kernel<T, LIM, 2, CPL, NF><<<grid, block, 0, s>>>(m, Uin, Un, out, sc); break;
+      default: stage1d_kernel<T, LIM, 3, CPL, NF><<<grid, block, 0, s>>>(m, Uin, Un, out, sc);
     }
   } else {
     dim3 grid((strips + STAGE_WARPS - 1) / STAGE_WARPS, (m.ny + TY - 1) / TY);
-    const size_t smem = STAGE_WARPS * Ring<T, CPL>::warp_bytes(stage);
+    const size_t smem = STAGE_WARPS * Ring<T, CPL, NF>::warp_bytes(stage);
     switch (stage) {
-      case 0: stage2d_kernel<T, LIM, 0, CPL, TY><<<grid, block, smem, s>>>(m, Uin, Un, out, sc); break;
-      case 1: stage2d_kernel<T, LIM, 1, CPL, TY><<<grid, block, smem, s>>>(m, Uin, Un, out, sc); break;
-      case 2: stage2d_kernel<T, LIM, 2, CPL, TY><<<grid, block, smem, s>>>(m, Uin, Un, out, sc); break;
-      default: stage2d_kernel<T, LIM, 3, CPL, TY><<<grid, block, smem, s>>>(m, Uin, Un, out, sc);
+      case 0: stage2d_kernel<T, LIM, 0, CPL, TY, NF><<<grid, block, smem, s>>>(m, Uin, Un, out, sc); break;
+      case 1: stage2d_kernel<T, LIM, 1, CPL, TY, NF><<<grid, block, smem, s>>>(m, Uin, Un, out, sc); break;
+      case 2: stage2d_kernel<T, LIM, 2, CPL, TY, NF><<<grid, block, smem, s>>>(m, Uin, Un, out, sc); break;
+      default: stage2d_kernel<T, LIM, 3, CPL, TY, NF><<<grid, block, smem, s>>>(m, Uin, Un, out, sc);
     }
   }
   return cudaGetLastError();
@@ -663,13 +679,14 @@ int batch_blocks_impl(int stage, int limiter) {
   }
 }
 
-template <typename T>
-cudaError_t launch_stage_impl(int stage, const MeshDesc& m, const T* Uin, const T* Un, T* out, Scalars* sc,
-                              cudaStream_t s) {
+// Stage launch for meshes with NF fields per cell.
+template <typename T, int NF>
+cudaError_t launch_stage_nf(int stage, const MeshDesc& m, const T* Uin, const T* Un, T* out, Scalars* sc,
+                            cudaStream_t s) {
   switch (m.limiter) {
-    case LIM_MINMOD: return launch_stage_lim<T, LIM_MINMOD>(stage, m, Uin, Un, out, sc, s);
-    case LIM_SWEBY: return launch_stage_lim<T, LIM_SWEBY>(stage, m, Uin, Un, out, sc, s);
-    default: return launch_stage_lim<T, LIM_VANLEER>(stage, m, Uin, Un, out, sc, s);
+    case LIM_MINMOD: return launch_stage_lim<T, LIM_MINMOD, NF>(stage, m, Uin, Un, out, sc, s);
+    case LIM_SWEBY: return launch_stage_lim<T, LIM_SWEBY, NF>(stage, m, Uin, Un, out, sc, s);
+    default: return launch_stage_lim<T, LIM_VANLEER, NF>(stage, m, Uin, Un, out, sc, s);
   }
 }
 

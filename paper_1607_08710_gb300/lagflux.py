@@ -18,6 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("LAGFLUX_LIB") or os.path.join(_HERE, "liblagflux.so")
 
 LF_OK, LF_ERR_ARG, LF_ERR_CUDA, LF_ERR_OOM, LF_ERR_NONPHYSICAL, LF_ERR_TIMEOUT, LF_ERR_STATE = range(7)
+MAX_SPECIES = 2  # LF_MAX_SPECIES
 LIMITERS = {"minmod": 0, "sweby": 1, "vanleer": 2}
 BCS = {"transmissive": 0, "periodic": 1}
 PRECISIONS = {"fp64": 0, "fp32": 1}
@@ -35,7 +36,7 @@ class lf_config(ctypes.Structure):
         ("riemann", ctypes.c_int32),
         ("device", ctypes.c_int32),
         ("time_order", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("nspecies", ctypes.c_int32),
         ("xmin", ctypes.c_double),
         ("xmax", ctypes.c_double),
         ("ymin", ctypes.c_double),
@@ -57,6 +58,10 @@ SIGNATURES = {
     "lf_set_primitive": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
     "lf_get_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
     "lf_get_primitive": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
+    "lf_set_partial_densities": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "lf_get_partial_densities": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "lf_set_mass_fractions": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "lf_get_mass_fractions": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "lf_step": (ctypes.c_int, [_vp, _P(_d)]),
     "lf_step_fixed": (ctypes.c_int, [_vp, _d]),
     "lf_run": (ctypes.c_int, [_vp, _d, _i32, _P(_i32), _P(_d)]),
@@ -121,11 +126,12 @@ class Config:
     ymax: float = 1.0
     device: int = 0
     time_order: int = 2  # 2: Heun (Sec. 4), 3: SSP-RK3
+    nspecies: int = 0  # transported mass fractions (Sec. 5), 0 .. MAX_SPECIES
 
     def to_c(self) -> lf_config:
         return lf_config(self.dim, self.nx, self.ny if self.dim == 2 else 1, LIMITERS[self.limiter], BCS[self.bc],
-                         PRECISIONS[self.precision], RIEMANN[self.riemann], self.device, self.time_order, 0,
-                         self.xmin, self.xmax, self.ymin, self.ymax, self.gamma, self.cfl, self.beta)
+                         PRECISIONS[self.precision], RIEMANN[self.riemann], self.device, self.time_order,
+                         self.nspecies, self.xmin, self.xmax, self.ymin, self.ymax, self.gamma, self.cfl, self.beta)
 
     @property
     def np_dtype(self):
@@ -224,6 +230,44 @@ class LagrangeFlux:
         self._check(_lib.lf_get_primitive(self._h, *ptrs, k))
         return out
 
+    # -- species (Sec. 5) -------------------------------------------------
+    def _species_buffer(self, a):
+        ny = self.cfg.ny if self.cfg.dim == 2 else 1
+        n = self.cfg.nspecies * self.cfg.nx * ny
+        p, k = _ptr_and_kind(a)
+        if int(np.prod(a.shape)) != n:
+            raise ValueError(f"species buffer has {int(np.prod(a.shape))} elements, expected {n}")
+        self._check_dtype(a)
+        return p, k
+
+    def _species_out(self, out):
+        if out is None:
+            ny = self.cfg.ny if self.cfg.dim == 2 else 1
+            out = np.empty((self.cfg.nspecies, ny, self.cfg.nx), dtype=self.cfg.np_dtype)
+        return out
+
+    def set_partial_densities(self, rho_y):
+        """rho_y: (nspecies, ny, nx) partial densities rho y_k."""
+        p, k = self._species_buffer(rho_y)
+        self._check(_lib.lf_set_partial_densities(self._h, p, k))
+
+    def get_partial_densities(self, out=None):
+        out = self._species_out(out)
+        p, k = self._species_buffer(out)
+        self._check(_lib.lf_get_partial_densities(self._h, p, k))
+        return out
+
+    def set_mass_fractions(self, y):
+        """y: (nspecies, ny, nx) mass fractions; rho y_k uses the current density."""
+        p, k = self._species_buffer(y)
+        self._check(_lib.lf_set_mass_fractions(self._h, p, k))
+
+    def get_mass_fractions(self, out=None):
+        out = self._species_out(out)
+        p, k = self._species_buffer(out)
+        self._check(_lib.lf_get_mass_fractions(self._h, p, k))
+        return out
+
     def step(self, return_dt: bool = False):
         if return_dt:
             dt = ctypes.c_double()
@@ -247,7 +291,8 @@ class LagrangeFlux:
         return t.value, s.value
 
     def conservation_sums(self) -> np.ndarray:
-        out = (ctypes.c_double * 4)()
+        """FP64 sums of the 4 + nspecies conservative fields."""
+        out = (ctypes.c_double * (4 + self.cfg.nspecies))()
         self._check(_lib.lf_conservation_sums(self._h, out))
         return np.array(out[:])
 

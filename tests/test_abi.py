@@ -64,7 +64,8 @@ def test_status_strings(lib):
 @pytest.mark.parametrize(
     "field,value",
     [("dim", 3), ("nx", 0), ("ny", 0), ("limiter", 7), ("bc", 2), ("precision", 5), ("riemann", 2), ("gamma", 1.0),
-     ("gamma", 3.5), ("cfl", 0.0), ("cfl", 1.5), ("beta", 2.5), ("xmax", 0.0), ("device", -1)],
+     ("gamma", 3.5), ("cfl", 0.0), ("cfl", 1.5), ("beta", 2.5), ("xmax", 0.0), ("device", -1), ("nspecies", 3),
+     ("nspecies", -1), ("time_order", 4)],
 )
 def test_init_rejects_bad_config_without_gpu(lib, field, value):
     cfg = lib.Config(nx=16, ny=16, limiter="sweby").to_c()
@@ -89,7 +90,14 @@ def test_null_arguments(lib):
     assert lib.lf_step(None, None) == lib.LF_ERR_ARG
     assert lib.lf_run(None, 0.0, 1, None, None) == lib.LF_ERR_ARG
     assert lib.lf_set_state(None, None, None, None, None, 0) == lib.LF_ERR_ARG
+    assert lib.lf_set_mass_fractions(None, None, 0) == lib.LF_ERR_ARG
+    assert lib.lf_get_partial_densities(None, None, 0) == lib.LF_ERR_ARG
     lib.lf_destroy(None)  # no-op
+
+
+def test_species_limit_matches_header(lib):
+    hdr = open(os.path.join(ROOT, "include", "lagflux.h")).read()
+    assert f"#define LF_MAX_SPECIES {lib.MAX_SPECIES}" in hdr
 
 
 def test_simulated_allocation_failure():
