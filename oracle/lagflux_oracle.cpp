@@ -17,12 +17,15 @@
 // Readings of points where the paper is silent (each is repeated in the
 // design notes):
 //   * CFL condition (Sec. 4, Heun step 1 only says "subject to some CFL
-//     condition"): dt = CFL / max_K[(|u_K|+c_K)/dx + (|v_K|+c_K)/dy] in 2D and
-//     dt = CFL / max_K[(|u_K|+c_K)/dx] in 1D, from U^n, the same dt for both
-//     stages; clipped to t_end - t when a final time is given.
+//     condition"): dt = CFL / max_K sum_d (|u_d,K| + c_K) / dx_d over the
+//     mesh's axes (1D: x; 2D: x, y; 3D: x, y, z), from U^n, the same dt for
+//     all stages; clipped to t_end - t when a final time is given.
+//   * Three dimensions (the finite-volume form of Sec. 4 is written for any
+//     polygonal/polyhedral cell): the same face formulas with a third flux
+//     direction; the state gains rho w, the primitive state w.
 //   * MUSCL (Sec. 4, eq. "sweby" and Heun step 2): limited undivided slopes of
-//     the primitive variables (rho, u, v, p), direction by direction, with
-//     face values q_i +/- sigma_i / 2.
+//     the primitive variables (rho, u, v, [w,] p), direction by direction,
+//     with face values q_i +/- sigma_i / 2.
 //   * Upwind edge value (eq. 12 and Heun step 4): the conservative vector
 //     rebuilt from the primitive state reconstructed on the upwind side,
 //     L if u* > 0, else R.
@@ -88,10 +91,10 @@ enum { RIEMANN_MAXC = 0, RIEMANN_PER_SIDE = 1 };
 enum { ORC_OK = 0, ORC_NONPHYSICAL = 1, ORC_ARG = 2 };
 
 constexpr int MAX_SPECIES = 8;
-constexpr int MAXF = 4 + MAX_SPECIES;  // largest number of transported fields
+constexpr int MAXF = 5 + MAX_SPECIES;  // largest number of transported fields
 
 struct OracleConfig {
-  int32_t dim;      // 1 or 2
+  int32_t dim;      // 1, 2 or 3
   int32_t nx, ny;   // cells (ny == 1 when dim == 1)
   int32_t limiter;  // LIM_*
   int32_t bc;       // BC_*
@@ -102,20 +105,29 @@ struct OracleConfig {
   double beta;      // Sweby coefficient, in [1, 2]
   int32_t time_order;  // 2: Heun (Sec. 4); 3: third-order SSP Runge-Kutta
   int32_t nspecies;    // transported mass fractions (Sec. 5), 0 .. MAX_SPECIES
+  int32_t nz;          // cells in z (1 unless dim == 3)
+  int32_t pad;
+  double dz;           // cell size in z (dim == 3)
 };
 
-// Fields per cell: (rho, rho u, rho v, rho E, rho y_1 .. rho y_nspecies).
-inline int nfields(const OracleConfig& c) { return 4 + c.nspecies; }
+// Velocity components carried: (u, v) in 1D and 2D (v = 0 in 1D), (u, v, w) in 3D.
+inline int nvel(const OracleConfig& c) { return c.dim == 3 ? 3 : 2; }
+// Index of rho E in the conservative vector and of p in the primitive one.
+inline int ien(const OracleConfig& c) { return 1 + nvel(c); }
+// Fields per cell: (rho, rho u, rho v, [rho w,] rho E, rho y_1 .. rho y_nspecies).
+inline int nfields(const OracleConfig& c) { return 2 + nvel(c) + c.nspecies; }
 
 bool config_ok(const OracleConfig* c) {
   if (!c) return false;
-  if (c->dim != 1 && c->dim != 2) return false;
-  if (c->nx < 1 || c->ny < 1) return false;
+  if (c->dim < 1 || c->dim > 3) return false;
+  if (c->nx < 1 || c->ny < 1 || c->nz < 1) return false;
   if (c->dim == 1 && c->ny != 1) return false;
+  if (c->dim < 3 && c->nz != 1) return false;
+  if (c->dim == 3 && !(c->dz > 0)) return false;
   if (c->limiter < 0 || c->limiter > 2) return false;
   if (c->bc < 0 || c->bc > 1) return false;
   if (c->riemann < 0 || c->riemann > 1) return false;
-  if (!(c->dx > 0) || (c->dim == 2 && !(c->dy > 0))) return false;
+  if (!(c->dx > 0) || (c->dim >= 2 && !(c->dy > 0))) return false;
   if (!(c->gamma > 1.0)) return false;
   if (c->time_order != 2 && c->time_order != 3) return false;
   if (c->nspecies < 0 || c->nspecies > MAX_SPECIES) return false;
@@ -124,30 +136,36 @@ bool config_ok(const OracleConfig* c) {
 
 // ---------------------------------------------------------------------------
 // Eq. (1): perfect-gas EOS p = (gamma-1) rho (E - |u|^2/2), c = sqrt(gamma p / rho).
-// Primitive vector q = (rho, u, v, p, y_1 ..); conservative
-// U = (rho, rho u, rho v, rho E, rho y_1 ..), nfields(c) entries each.
+// Primitive vector q = (rho, u, v, [w,] p, y_1 ..); conservative
+// U = (rho, rho u, rho v, [rho w,] rho E, rho y_1 ..), nfields(c) entries each.
 // ---------------------------------------------------------------------------
 template <class S>
 void prim_from_cons(const OracleConfig& c, const S U[], S q[]) {
+  const int nv = nvel(c), e = ien(c);
   S rho = U[0];
-  S u = U[1] / rho;
-  S v = U[2] / rho;
-  S E = U[3] / rho;
+  S kin = S(0.0);  // |u|^2
+  for (int d = 0; d < nv; ++d) {
+    q[1 + d] = U[1 + d] / rho;
+    kin = kin + q[1 + d] * q[1 + d];
+  }
+  S E = U[e] / rho;
   q[0] = rho;
-  q[1] = u;
-  q[2] = v;
-  q[3] = (c.gamma - 1.0) * rho * (E - 0.5 * (u * u + v * v));
-  for (int k = 0; k < c.nspecies; ++k) q[4 + k] = U[4 + k] / rho;
+  q[e] = (c.gamma - 1.0) * rho * (E - 0.5 * kin);
+  for (int k = 0; k < c.nspecies; ++k) q[e + 1 + k] = U[e + 1 + k] / rho;
 }
 
 template <class S>
 void cons_from_prim(const OracleConfig& c, const S q[], S U[]) {
-  S rho = q[0], u = q[1], v = q[2], p = q[3];
+  const int nv = nvel(c), e = ien(c);
+  S rho = q[0], p = q[e];
+  S kin = S(0.0);
   U[0] = rho;
-  U[1] = rho * u;
-  U[2] = rho * v;
-  U[3] = p / (c.gamma - 1.0) + 0.5 * rho * (u * u + v * v);
-  for (int k = 0; k < c.nspecies; ++k) U[4 + k] = rho * q[4 + k];
+  for (int d = 1; d <= nv; ++d) {
+    U[d] = rho * q[d];
+    kin = kin + q[d] * q[d];
+  }
+  U[e] = p / (c.gamma - 1.0) + 0.5 * rho * kin;
+  for (int k = 0; k < c.nspecies; ++k) U[e + 1 + k] = rho * q[e + 1 + k];
 }
 
 template <class S>
@@ -199,27 +217,29 @@ void interface_solve(const OracleConfig& c, const S& rL, const S& uL, const S& p
 
 // ---------------------------------------------------------------------------
 // Eq. (12) with the upwinding of Sec. 4 (Heun steps 3-5): for a face with unit
-// normal nu along axis `dir` (0 = x, 1 = y), pointing from L to R,
-//   Phi = U_A (u* ) + (0, p* nu_x, p* nu_y, p* u*),
+// normal nu along axis `dir` (0 = x, 1 = y, 2 = z), pointing from L to R,
+//   Phi = U_A (u* ) + (0, p* nu, p* u*),
 // U_A = U(q_L) if u* > 0 else U(q_R).  The species rows of Phi are
 // (rho y_k)_A u*, with no pressure term.
 // ---------------------------------------------------------------------------
 template <class S>
 void face_flux(const OracleConfig& c, int dir, const S qL[], const S qR[], S F[]) {
+  const int e = ien(c);
   S pstar, ustar;
-  interface_solve(c, qL[0], qL[1 + dir], qL[3], qR[0], qR[1 + dir], qR[3], pstar, ustar);
+  interface_solve(c, qL[0], qL[1 + dir], qL[e], qR[0], qR[1 + dir], qR[e], pstar, ustar);
   const S* qup = (val(ustar) > 0.0) ? qL : qR;
   S Uup[MAXF];
   cons_from_prim(c, qup, Uup);
   for (int l = 0; l < nfields(c); ++l) F[l] = Uup[l] * ustar;
   F[1 + dir] = F[1 + dir] + pstar;
-  F[3] = F[3] + pstar * ustar;
+  F[e] = F[e] + pstar * ustar;
 }
 
 // ---------------------------------------------------------------------------
-// Mesh bookkeeping: planes of nx*ny values, x fastest (index j*nx + i).
-// Ghost-extended primitive arrays have (nx+4) x (ny+4) cells in 2D and
-// (nx+4) cells in 1D, offset by G = 2.
+// Mesh bookkeeping: planes of nx*ny*nz values, x fastest (index
+// (k*ny + j)*nx + i).  Ghost-extended primitive arrays carry G = 2 layers on
+// each active axis (x; x, y; or x, y, z).  Inactive axes have one cell, no
+// ghosts and size 1.
 // ---------------------------------------------------------------------------
 const int G = 2;
 
@@ -234,13 +254,33 @@ inline int wrap_index(int i, int n, int bc) {
 template <class S>
 struct Mesh {
   const OracleConfig& c;
-  int nx, ny, gx, gy;  // interior and ghost-extended extents
-  explicit Mesh(const OracleConfig& cfg)
-      : c(cfg), nx(cfg.nx), ny(cfg.ny), gx(cfg.nx + 2 * G), gy(cfg.dim == 2 ? cfg.ny + 2 * G : 1) {}
-  size_t ncell() const { return (size_t)nx * ny; }
-  // ghost-extended index of interior-relative cell (i, j)
-  size_t gidx(int i, int j) const {
-    return (size_t)(c.dim == 2 ? j + G : 0) * gx + (i + G);
+  int n[3];      // cells per axis
+  int g[3];      // ghost layers per axis
+  int ext[3];    // ghost-extended extents
+  double h[3];   // cell sizes
+  explicit Mesh(const OracleConfig& cfg) : c(cfg) {
+    n[0] = cfg.nx;
+    n[1] = cfg.ny;
+    n[2] = cfg.nz;
+    h[0] = cfg.dx;
+    h[1] = cfg.dim >= 2 ? cfg.dy : 1.0;
+    h[2] = cfg.dim == 3 ? cfg.dz : 1.0;
+    for (int d = 0; d < 3; ++d) {
+      g[d] = d < cfg.dim ? G : 0;
+      ext[d] = n[d] + 2 * g[d];
+    }
+  }
+  size_t ncell() const { return (size_t)n[0] * n[1] * n[2]; }
+  size_t cell(int i, int j, int k) const { return ((size_t)k * n[1] + j) * n[0] + i; }
+  // ghost-extended index of interior-relative cell (i, j, k)
+  size_t gidx(int i, int j, int k) const {
+    return ((size_t)(k + g[2]) * ext[1] + (j + g[1])) * ext[0] + (i + g[0]);
+  }
+  // Faces normal to axis d: n[d] + 1 of them along d; face (i, j, k) lies
+  // between the cell one step back along d and cell (i, j, k).
+  size_t nfaces(int d) const { return (size_t)(n[0] + (d == 0)) * (n[1] + (d == 1)) * (n[2] + (d == 2)); }
+  size_t fidx(int d, int i, int j, int k) const {
+    return ((size_t)k * (n[1] + (d == 1)) + j) * (n[0] + (d == 0)) + i;
   }
 };
 
@@ -249,107 +289,107 @@ template <class S>
 bool build_primitives(const Mesh<S>& m, const std::vector<S> U[], std::vector<S> qg[]) {
   const OracleConfig& c = m.c;
   const int nf = nfields(c);
-  for (int l = 0; l < nf; ++l) qg[l].assign((size_t)m.gx * m.gy, S(0.0));
+  for (int l = 0; l < nf; ++l) qg[l].assign((size_t)m.ext[0] * m.ext[1] * m.ext[2], S(0.0));
   bool physical = true;
-  int jlo = (c.dim == 2) ? -G : 0, jhi = (c.dim == 2) ? m.ny + G : 1;
-  for (int j = jlo; j < jhi; ++j) {
-    for (int i = -G; i < m.nx + G; ++i) {
-      // A ghost cell takes the primitive state of the interior cell it maps to.
-      int si = wrap_index(i, m.nx, c.bc);
-      int sj = (c.dim == 2) ? wrap_index(j, m.ny, c.bc) : 0;
-      size_t s = (size_t)sj * m.nx + si;
-      S Uc[MAXF], q[MAXF];
-      for (int l = 0; l < nf; ++l) Uc[l] = U[l][s];
-      prim_from_cons(c, Uc, q);
-      if (!(val(q[0]) > 0.0) || !(val(q[3]) > 0.0)) physical = false;
-      size_t g = m.gidx(i, j);
-      for (int l = 0; l < nf; ++l) qg[l][g] = q[l];
-    }
-  }
+  for (int k = -m.g[2]; k < m.n[2] + m.g[2]; ++k)
+    for (int j = -m.g[1]; j < m.n[1] + m.g[1]; ++j)
+      for (int i = -m.g[0]; i < m.n[0] + m.g[0]; ++i) {
+        // A ghost cell takes the primitive state of the interior cell it maps to.
+        size_t s = m.cell(wrap_index(i, m.n[0], c.bc), wrap_index(j, m.n[1], c.bc), wrap_index(k, m.n[2], c.bc));
+        S Uc[MAXF], q[MAXF];
+        for (int l = 0; l < nf; ++l) Uc[l] = U[l][s];
+        prim_from_cons(c, Uc, q);
+        if (!(val(q[0]) > 0.0) || !(val(q[ien(c)]) > 0.0)) physical = false;
+        size_t gi = m.gidx(i, j, k);
+        for (int l = 0; l < nf; ++l) qg[l][gi] = q[l];
+      }
   return physical;
 }
 
-// All face fluxes of a state (Heun steps 2-5, or 7-10).
-// Fx has (nx+1) x ny faces (face f of row j between cells f-1 and f),
-// Fy has nx x (ny+1) faces (face g of column i between cells g-1 and g).
+// All face fluxes of a state (Heun steps 2-5, or 7-10): F[d][l] holds field
+// l's flux through every face normal to axis d (indexed by Mesh::fidx).
 template <class S>
-bool all_face_fluxes(const Mesh<S>& m, const std::vector<S> U[], std::vector<S> Fx[],
-                     std::vector<S> Fy[]) {
+bool all_face_fluxes(const Mesh<S>& m, const std::vector<S> U[], std::vector<S> F[3][MAXF]) {
   const OracleConfig& c = m.c;
   const int nf = nfields(c);
   std::vector<S> qg[MAXF];
   bool physical = build_primitives(m, U, qg);
-  auto q_at = [&](int l, int i, int j) -> S { return qg[l][m.gidx(i, j)]; };
-
-  // x-faces
-  for (int l = 0; l < nf; ++l) Fx[l].assign((size_t)(m.nx + 1) * m.ny, S(0.0));
-  for (int j = 0; j < m.ny; ++j) {
-    for (int f = 0; f <= m.nx; ++f) {
-      int iL = f - 1, iR = f;
-      S qL[MAXF], qR[MAXF];
-      for (int l = 0; l < nf; ++l) {
-        S sL = limiter(c, q_at(l, iL, j) - q_at(l, iL - 1, j), q_at(l, iL + 1, j) - q_at(l, iL, j));
-        S sR = limiter(c, q_at(l, iR, j) - q_at(l, iR - 1, j), q_at(l, iR + 1, j) - q_at(l, iR, j));
-        qL[l] = q_at(l, iL, j) + 0.5 * sL;
-        qR[l] = q_at(l, iR, j) - 0.5 * sR;
-      }
-      S F[MAXF];
-      face_flux(c, 0, qL, qR, F);
-      for (int l = 0; l < nf; ++l) Fx[l][(size_t)j * (m.nx + 1) + f] = F[l];
-    }
-  }
-  // y-faces
-  if (c.dim == 2) {
-    for (int l = 0; l < nf; ++l) Fy[l].assign((size_t)m.nx * (m.ny + 1), S(0.0));
-    for (int g = 0; g <= m.ny; ++g) {
-      for (int i = 0; i < m.nx; ++i) {
-        int jL = g - 1, jR = g;
-        S qL[MAXF], qR[MAXF];
-        for (int l = 0; l < nf; ++l) {
-          S sL = limiter(c, q_at(l, i, jL) - q_at(l, i, jL - 1), q_at(l, i, jL + 1) - q_at(l, i, jL));
-          S sR = limiter(c, q_at(l, i, jR) - q_at(l, i, jR - 1), q_at(l, i, jR + 1) - q_at(l, i, jR));
-          qL[l] = q_at(l, i, jL) + 0.5 * sL;
-          qR[l] = q_at(l, i, jR) - 0.5 * sR;
+  // primitive l of the cell s steps along axis d from cell (i, j, k)
+  auto q_at = [&](int l, int d, int s, int i, int j, int k) -> S {
+    int o[3] = {i, j, k};
+    o[d] += s;
+    return qg[l][m.gidx(o[0], o[1], o[2])];
+  };
+  for (int d = 0; d < c.dim; ++d) {
+    for (int l = 0; l < nf; ++l) F[d][l].assign(m.nfaces(d), S(0.0));
+    int e[3] = {m.n[0], m.n[1], m.n[2]};
+    e[d] += 1;
+    for (int k = 0; k < e[2]; ++k)
+      for (int j = 0; j < e[1]; ++j)
+        for (int i = 0; i < e[0]; ++i) {
+          // left cell: one step back along d; right cell: (i, j, k)
+          S qL[MAXF], qR[MAXF];
+          for (int l = 0; l < nf; ++l) {
+            S sL = limiter(c, q_at(l, d, -1, i, j, k) - q_at(l, d, -2, i, j, k),
+                           q_at(l, d, 0, i, j, k) - q_at(l, d, -1, i, j, k));
+            S sR = limiter(c, q_at(l, d, 0, i, j, k) - q_at(l, d, -1, i, j, k),
+                           q_at(l, d, 1, i, j, k) - q_at(l, d, 0, i, j, k));
+            qL[l] = q_at(l, d, -1, i, j, k) + 0.5 * sL;
+            qR[l] = q_at(l, d, 0, i, j, k) - 0.5 * sR;
+          }
+          S Fv[MAXF];
+          face_flux(c, d, qL, qR, Fv);
+          for (int l = 0; l < nf; ++l) F[d][l][m.fidx(d, i, j, k)] = Fv[l];
         }
-        S F[MAXF];
-        face_flux(c, 1, qL, qR, F);
-        for (int l = 0; l < nf; ++l) Fy[l][(size_t)g * m.nx + i] = F[l];
-      }
-    }
   }
   return physical;
 }
 
 // Sum over the faces of cell K of |A| Phi_A . nu_A (outward), divided by |K|
 // (Sec. 4, semi-discrete scheme after eq. 11).  Fluxes are stored with the
-// normal pointing to +x (+y); the left (bottom) face enters with a minus sign.
+// normal pointing along +d; the face behind the cell enters with a minus sign.
 template <class S>
-S flux_balance(const Mesh<S>& m, const std::vector<S>& Fx, const std::vector<S>& Fy, int i, int j) {
-  const OracleConfig& c = m.c;
-  if (c.dim == 1) {
-    double K = c.dx, A = 1.0;
-    return (A * Fx[i + 1] - A * Fx[i]) / K;
+S flux_balance(const Mesh<S>& m, const std::vector<S> F[3][MAXF], int l, int i, int j, int k) {
+  const double K = m.h[0] * m.h[1] * m.h[2];
+  S acc = S(0.0);
+  for (int d = 0; d < m.c.dim; ++d) {
+    const double A = m.h[(d + 1) % 3] * m.h[(d + 2) % 3];
+    int hi[3] = {i, j, k};
+    hi[d] += 1;
+    S ahead = F[d][l][m.fidx(d, hi[0], hi[1], hi[2])], behind = F[d][l][m.fidx(d, i, j, k)];
+    acc = acc + A * ahead - A * behind;
   }
-  double K = c.dx * c.dy, Ax = c.dy, Ay = c.dx;
-  S east = Fx[(size_t)j * (m.nx + 1) + i + 1], west = Fx[(size_t)j * (m.nx + 1) + i];
-  S north = Fy[(size_t)(j + 1) * m.nx + i], south = Fy[(size_t)j * m.nx + i];
-  return (Ax * east - Ax * west + Ay * north - Ay * south) / K;
+  return acc / K;
 }
 
 // Heun step 1 under the CFL reading stated at the top of this file.
 double cfl_dt(const OracleConfig& c, const std::vector<double> U[]) {
+  Mesh<double> m(c);
   double smax = 0.0;
-  size_t n = (size_t)c.nx * c.ny;
-  for (size_t k = 0; k < n; ++k) {
+  for (size_t k = 0; k < m.ncell(); ++k) {
     double Uc[MAXF], q[MAXF];
     for (int l = 0; l < nfields(c); ++l) Uc[l] = U[l][k];
     prim_from_cons(c, Uc, q);
-    double a = sound_speed(c, q[0], q[3]);
-    double s = (std::fabs(q[1]) + a) / c.dx;
-    if (c.dim == 2) s += (std::fabs(q[2]) + a) / c.dy;
+    double a = sound_speed(c, q[0], q[ien(c)]);
+    double s = 0.0;
+    for (int d = 0; d < c.dim; ++d) s += (std::fabs(q[1 + d]) + a) / m.h[d];
     if (s > smax) smax = s;
   }
   return c.cfl / smax;
+}
+
+// Positivity of a state (rho > 0 and p > 0 in every cell).
+template <class S>
+bool state_physical(const Mesh<S>& m, const std::vector<S> U[]) {
+  const OracleConfig& c = m.c;
+  bool ok = true;
+  for (size_t k = 0; k < m.ncell(); ++k) {
+    S Uc[MAXF], q[MAXF];
+    for (int l = 0; l < nfields(c); ++l) Uc[l] = U[l][k];
+    prim_from_cons(c, Uc, q);
+    if (!(val(q[0]) > 0.0) || !(val(q[ien(c)]) > 0.0)) ok = false;
+  }
+  return ok;
 }
 
 // One Heun step (Sec. 4, steps 2-11) with a given dt.
@@ -357,32 +397,27 @@ template <class S>
 bool heun_step(const OracleConfig& c, std::vector<S> U[], double dt) {
   Mesh<S> m(c);
   const int nf = nfields(c);
-  std::vector<S> Fxn[MAXF], Fyn[MAXF], Fxs[MAXF], Fys[MAXF], Us[MAXF];
-  bool ok = all_face_fluxes(m, U, Fxn, Fyn);  // steps 2-5
+  std::vector<S> Fn[3][MAXF], Fs[3][MAXF], Us[MAXF];
+  bool ok = all_face_fluxes(m, U, Fn);  // steps 2-5
   for (int l = 0; l < nf; ++l) Us[l].resize(m.ncell());
-  for (int j = 0; j < m.ny; ++j)  // step 6: predicted states
-    for (int i = 0; i < m.nx; ++i) {
-      size_t k = (size_t)j * m.nx + i;
-      for (int l = 0; l < nf; ++l) Us[l][k] = U[l][k] - dt * flux_balance(m, Fxn[l], Fyn[l], i, j);
-    }
-  ok = all_face_fluxes(m, Us, Fxs, Fys) && ok;  // steps 7-10
-  for (int j = 0; j < m.ny; ++j)  // step 11: averaged fluxes
-    for (int i = 0; i < m.nx; ++i) {
-      size_t k = (size_t)j * m.nx + i;
-      for (int l = 0; l < nf; ++l) {
-        S bn = flux_balance(m, Fxn[l], Fyn[l], i, j);
-        S bs = flux_balance(m, Fxs[l], Fys[l], i, j);
-        U[l][k] = U[l][k] - dt * ((bn + bs) / 2.0);
+  for (int k = 0; k < m.n[2]; ++k)  // step 6: predicted states
+    for (int j = 0; j < m.n[1]; ++j)
+      for (int i = 0; i < m.n[0]; ++i) {
+        size_t x = m.cell(i, j, k);
+        for (int l = 0; l < nf; ++l) Us[l][x] = U[l][x] - dt * flux_balance(m, Fn, l, i, j, k);
       }
-    }
-  // Positivity of the new state.
-  for (size_t k = 0; k < m.ncell(); ++k) {
-    S Uc[MAXF], q[MAXF];
-    for (int l = 0; l < nf; ++l) Uc[l] = U[l][k];
-    prim_from_cons(c, Uc, q);
-    if (!(val(q[0]) > 0.0) || !(val(q[3]) > 0.0)) ok = false;
-  }
-  return ok;
+  ok = all_face_fluxes(m, Us, Fs) && ok;  // steps 7-10
+  for (int k = 0; k < m.n[2]; ++k)  // step 11: averaged fluxes
+    for (int j = 0; j < m.n[1]; ++j)
+      for (int i = 0; i < m.n[0]; ++i) {
+        size_t x = m.cell(i, j, k);
+        for (int l = 0; l < nf; ++l) {
+          S bn = flux_balance(m, Fn, l, i, j, k);
+          S bs = flux_balance(m, Fs, l, i, j, k);
+          U[l][x] = U[l][x] - dt * ((bn + bs) / 2.0);
+        }
+      }
+  return state_physical(m, U) && ok;
 }
 
 // Third-order strong-stability-preserving Runge-Kutta step of Shu and Osher
@@ -396,36 +431,33 @@ template <class S>
 bool ssprk3_step(const OracleConfig& c, std::vector<S> U[], double dt) {
   Mesh<S> m(c);
   const int nf = nfields(c);
-  std::vector<S> Fx[MAXF], Fy[MAXF], U1[MAXF], U2[MAXF];
-  bool ok = all_face_fluxes(m, U, Fx, Fy);
+  std::vector<S> F[3][MAXF], U1[MAXF], U2[MAXF];
+  bool ok = all_face_fluxes(m, U, F);
   for (int l = 0; l < nf; ++l) U1[l].resize(m.ncell());
-  for (int j = 0; j < m.ny; ++j)
-    for (int i = 0; i < m.nx; ++i) {
-      size_t k = (size_t)j * m.nx + i;
-      for (int l = 0; l < nf; ++l) U1[l][k] = U[l][k] - dt * flux_balance(m, Fx[l], Fy[l], i, j);
-    }
-  ok = all_face_fluxes(m, U1, Fx, Fy) && ok;
+  for (int k = 0; k < m.n[2]; ++k)
+    for (int j = 0; j < m.n[1]; ++j)
+      for (int i = 0; i < m.n[0]; ++i) {
+        size_t x = m.cell(i, j, k);
+        for (int l = 0; l < nf; ++l) U1[l][x] = U[l][x] - dt * flux_balance(m, F, l, i, j, k);
+      }
+  ok = all_face_fluxes(m, U1, F) && ok;
   for (int l = 0; l < nf; ++l) U2[l].resize(m.ncell());
-  for (int j = 0; j < m.ny; ++j)
-    for (int i = 0; i < m.nx; ++i) {
-      size_t k = (size_t)j * m.nx + i;
-      for (int l = 0; l < nf; ++l)
-        U2[l][k] = 0.75 * U[l][k] + 0.25 * (U1[l][k] - dt * flux_balance(m, Fx[l], Fy[l], i, j));
-    }
-  ok = all_face_fluxes(m, U2, Fx, Fy) && ok;
-  for (int j = 0; j < m.ny; ++j)
-    for (int i = 0; i < m.nx; ++i) {
-      size_t k = (size_t)j * m.nx + i;
-      for (int l = 0; l < nf; ++l)
-        U[l][k] = U[l][k] / 3.0 + (2.0 / 3.0) * (U2[l][k] - dt * flux_balance(m, Fx[l], Fy[l], i, j));
-    }
-  for (size_t k = 0; k < m.ncell(); ++k) {
-    S Uc[MAXF], q[MAXF];
-    for (int l = 0; l < nf; ++l) Uc[l] = U[l][k];
-    prim_from_cons(c, Uc, q);
-    if (!(val(q[0]) > 0.0) || !(val(q[3]) > 0.0)) ok = false;
-  }
-  return ok;
+  for (int k = 0; k < m.n[2]; ++k)
+    for (int j = 0; j < m.n[1]; ++j)
+      for (int i = 0; i < m.n[0]; ++i) {
+        size_t x = m.cell(i, j, k);
+        for (int l = 0; l < nf; ++l)
+          U2[l][x] = 0.75 * U[l][x] + 0.25 * (U1[l][x] - dt * flux_balance(m, F, l, i, j, k));
+      }
+  ok = all_face_fluxes(m, U2, F) && ok;
+  for (int k = 0; k < m.n[2]; ++k)
+    for (int j = 0; j < m.n[1]; ++j)
+      for (int i = 0; i < m.n[0]; ++i) {
+        size_t x = m.cell(i, j, k);
+        for (int l = 0; l < nf; ++l)
+          U[l][x] = U[l][x] / 3.0 + (2.0 / 3.0) * (U2[l][x] - dt * flux_balance(m, F, l, i, j, k));
+      }
+  return state_physical(m, U) && ok;
 }
 
 template <class S>
@@ -434,11 +466,11 @@ bool time_step(const OracleConfig& c, std::vector<S> U[], double dt) {
 }
 
 void load_planes(const OracleConfig& c, const double* src, std::vector<double> U[]) {
-  size_t n = (size_t)c.nx * c.ny;
+  size_t n = (size_t)c.nx * c.ny * c.nz;
   for (int l = 0; l < nfields(c); ++l) U[l].assign(src + l * n, src + (l + 1) * n);
 }
 void store_planes(const OracleConfig& c, const std::vector<double> U[], double* dst) {
-  size_t n = (size_t)c.nx * c.ny;
+  size_t n = (size_t)c.nx * c.ny * c.nz;
   for (int l = 0; l < nfields(c); ++l) std::memcpy(dst + l * n, U[l].data(), n * sizeof(double));
 }
 
@@ -480,7 +512,7 @@ int oracle_face_flux(const OracleConfig* c, int dir, int64_t n, const double* qL
 
 int oracle_prim_to_cons(const OracleConfig* c, const double* q, double* U) {
   if (!config_ok(c)) return ORC_ARG;
-  size_t n = (size_t)c->nx * c->ny;
+  size_t n = (size_t)c->nx * c->ny * c->nz;
   const int nf = nfields(*c);
   for (size_t k = 0; k < n; ++k) {
     double qc[MAXF] = {}, Uc[MAXF];
@@ -493,7 +525,7 @@ int oracle_prim_to_cons(const OracleConfig* c, const double* q, double* U) {
 
 int oracle_cons_to_prim(const OracleConfig* c, const double* U, double* q) {
   if (!config_ok(c)) return ORC_ARG;
-  size_t n = (size_t)c->nx * c->ny;
+  size_t n = (size_t)c->nx * c->ny * c->nz;
   const int nf = nfields(*c);
   for (size_t k = 0; k < n; ++k) {
     double Uc[MAXF] = {}, qc[MAXF];
@@ -516,15 +548,15 @@ int oracle_dt(const OracleConfig* c, const double* Uin, double* dt) {
 // scheme after eq. (11).
 int oracle_residual(const OracleConfig* c, const double* Uin, double* LU) {
   if (!config_ok(c) || !Uin || !LU) return ORC_ARG;
-  std::vector<double> U[MAXF], Fx[MAXF], Fy[MAXF];
+  std::vector<double> U[MAXF], F[3][MAXF];
   load_planes(*c, Uin, U);
   Mesh<double> m(*c);
-  bool ok = all_face_fluxes(m, U, Fx, Fy);
+  bool ok = all_face_fluxes(m, U, F);
   size_t n = m.ncell();
-  for (int j = 0; j < m.ny; ++j)
-    for (int i = 0; i < m.nx; ++i)
-      for (int l = 0; l < nfields(*c); ++l)
-        LU[l * n + (size_t)j * m.nx + i] = -flux_balance(m, Fx[l], Fy[l], i, j);
+  for (int k = 0; k < m.n[2]; ++k)
+    for (int j = 0; j < m.n[1]; ++j)
+      for (int i = 0; i < m.n[0]; ++i)
+        for (int l = 0; l < nfields(*c); ++l) LU[l * n + m.cell(i, j, k)] = -flux_balance(m, F, l, i, j, k);
   return ok ? ORC_OK : ORC_NONPHYSICAL;
 }
 
@@ -567,7 +599,7 @@ int oracle_run(const OracleConfig* c, double* Uio, int32_t max_steps, double t0,
 int oracle_run_tangent(const OracleConfig* c, const double* q0, const double* dq0, int32_t nsteps,
                        const double* dts, double* U_out, double* dU_out) {
   if (!config_ok(c) || !q0 || !dq0 || !dts || nsteps < 0) return ORC_ARG;
-  size_t n = (size_t)c->nx * c->ny;
+  size_t n = (size_t)c->nx * c->ny * c->nz;
   const int nf = nfields(*c);
   std::vector<Dual> U[MAXF];
   for (int l = 0; l < nf; ++l) U[l].resize(n);

@@ -8,7 +8,8 @@ benchmark may import this module; the product package never does.
 Arrays use the oracle's own layout: a state is a float64 array of shape
 (4 + nspecies, ny, nx) holding (rho, rho u, rho v, rho E, rho y_1 ..) -- or
 (rho, u, v, p, y_1 ..) for primitive states -- with x fastest.  1D problems
-have ny == 1.
+have ny == 1.  3D states have shape (5 + nspecies, nz, ny, nx) and hold
+(rho, rho u, rho v, rho w, rho E, rho y_1 ..) or (rho, u, v, w, p, y_1 ..).
 
 Parity status of each function (see the pins in tests/test_oracle_*.py):
   limiter, interface_solve, face_flux, prim/cons, dt, residual, run,
@@ -58,6 +59,9 @@ class _Cfg(ctypes.Structure):
         ("beta", ctypes.c_double),
         ("time_order", ctypes.c_int32),
         ("nspecies", ctypes.c_int32),
+        ("nz", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+        ("dz", ctypes.c_double),
     ]
 
 
@@ -78,17 +82,26 @@ class OracleConfig:
     ly: float = 1.0
     time_order: int = 2  # 2: Heun (Sec. 4), 3: third-order SSP Runge-Kutta
     nspecies: int = 0  # transported mass fractions y_k (Sec. 5)
+    nz: int = 1
+    lz: float = 1.0
 
     @property
     def nfields(self) -> int:
-        return 4 + self.nspecies
+        return (5 if self.dim == 3 else 4) + self.nspecies
+
+    @property
+    def shape(self) -> tuple:
+        """Shape of one plane: (ny, nx), or (nz, ny, nx) in 3D."""
+        ny = self.ny if self.dim >= 2 else 1
+        return (self.nz, ny, self.nx) if self.dim == 3 else (ny, self.nx)
 
     def to_c(self) -> _Cfg:
-        ny = self.ny if self.dim == 2 else 1
+        ny = self.ny if self.dim >= 2 else 1
+        nz = self.nz if self.dim == 3 else 1
         return _Cfg(
             self.dim, self.nx, ny, LIMITERS[self.limiter], BCS[self.bc], RIEMANN[self.riemann],
-            self.lx / self.nx, self.ly / ny if self.dim == 2 else 1.0, self.gamma, self.cfl, self.beta,
-            self.time_order, self.nspecies,
+            self.lx / self.nx, self.ly / ny if self.dim >= 2 else 1.0, self.gamma, self.cfl, self.beta,
+            self.time_order, self.nspecies, nz, 0, self.lz / nz if self.dim == 3 else 1.0,
         )
 
 
@@ -219,9 +232,9 @@ def face_flux(cfg: OracleConfig, direction: int, qL, qR) -> np.ndarray:
 # ---------------------------------------------------------------------------
 def _state(cfg: OracleConfig, U) -> np.ndarray:
     U = _f64(U)
-    ny = cfg.ny if cfg.dim == 2 else 1
-    if U.shape != (cfg.nfields, ny, cfg.nx):
-        U = U.reshape(cfg.nfields, ny, cfg.nx)
+    shape = (cfg.nfields,) + cfg.shape
+    if U.shape != shape:
+        U = U.reshape(shape)
     return np.ascontiguousarray(U)
 
 

@@ -17,7 +17,10 @@ Workloads:
   * transported mass fractions (Sec. 5): a smooth scalar carried by a uniform
     flow (exact solution: a translation), a seeded three-region, two-material
     problem on the (0, 7) x (0, 3) vessel of the paper's triple-point case,
-    and material indicators of the shear layer.
+    and material indicators of the shear layer;
+  * 3D: seeded eight-octant Riemann problems, a smooth density wave carried
+    along the main diagonal, and a three-dimensional shear layer.
+3D fields have shape (nz, ny, nx).
 """
 from __future__ import annotations
 
@@ -43,15 +46,17 @@ class Primitive:
     u: np.ndarray
     v: np.ndarray
     p: np.ndarray
-    y: np.ndarray | None = None  # mass fractions, shape (nspecies, ny, nx)
+    y: np.ndarray | None = None  # mass fractions, shape (nspecies,) + field shape
+    w: np.ndarray | None = None  # third velocity component (3D fields only)
 
     @property
     def nspecies(self) -> int:
         return 0 if self.y is None else int(self.y.shape[0])
 
     def stack(self) -> np.ndarray:
-        """(4 + nspecies, ny, nx): rho, u, v, p, then y_1 .. y_nspecies."""
-        planes = [self.rho, self.u, self.v, self.p]
+        """(4 + nspecies, ny, nx): rho, u, v, p, then y_1 .. y_nspecies;
+        3D: (5 + nspecies, nz, ny, nx) with w after v."""
+        planes = [self.rho, self.u, self.v] + ([self.w] if self.w is not None else []) + [self.p]
         if self.y is not None:
             planes += list(self.y)
         return np.stack(planes).astype(np.float64)
@@ -180,12 +185,12 @@ def batched_sizes(nprob: int, seed: int = 0, lo: int = 64, hi: int = 1024) -> np
 
 
 def with_species(prim: Primitive, y) -> Primitive:
-    """The same flow carrying the mass fractions y (shape (nspecies, ny, nx))."""
+    """The same flow carrying the mass fractions y (shape (nspecies,) + field shape)."""
     y = np.asarray(y, dtype=np.float64)
-    if y.ndim == 2:
+    if y.ndim == prim.rho.ndim:
         y = y[None]
     assert y.shape[1:] == prim.shape
-    return Primitive(prim.rho, prim.u, prim.v, prim.p, y.copy())
+    return Primitive(prim.rho, prim.u, prim.v, prim.p, y.copy(), prim.w)
 
 
 def advected_scalar_1d(nx: int, t: float = 0.0) -> Primitive:
@@ -264,3 +269,64 @@ def shear_layer_tracers(nx: int, ny: int | None = None, seed: int = 0, nspecies:
     for k in range(2, nspecies):
         ys.append(0.5 + 0.4 * smooth_perturbation(nx, ny, seed=seed * 31 + k))
     return with_species(kh, np.stack(ys[:nspecies]))
+
+
+# ---------------------------------------------------------------------------
+# 3D fields, shape (nz, ny, nx) on the unit cube unless stated
+# ---------------------------------------------------------------------------
+def _grid3(nx: int, ny: int, nz: int):
+    x = cell_centres(nx)[None, None, :]
+    y = cell_centres(ny)[None, :, None]
+    z = cell_centres(nz)[:, None, None]
+    return x, y, z
+
+
+def octant_states(seed: int) -> np.ndarray:
+    """Eight constant states, rows for octants o = 4 [z >= 1/2] + 2 [y >= 1/2] + [x >= 1/2],
+    columns (rho, u, v, w, p): rho ~ U[0.5, 1.5], u, v, w ~ U[-0.75, 0.75],
+    p ~ U[0.1, 1.0], drawn octant by octant in that order."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((8, 5))
+    for o in range(8):
+        out[o, 0] = rng.uniform(0.5, 1.5)
+        out[o, 1:4] = [rng.uniform(-0.75, 0.75) for _ in range(3)]
+        out[o, 4] = rng.uniform(0.1, 1.0)
+    return out
+
+
+def octant(nx: int, ny: int | None = None, nz: int | None = None, seed: int = 0) -> Primitive:
+    """Eight-octant 3D Riemann problem on [0, 1]^3, split at x = y = z = 0.5."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    st = octant_states(seed)
+    x, y, z = _grid3(nx, ny, nz)
+    o = 4 * (z >= 0.5) + 2 * (y >= 0.5) + (x >= 0.5)
+    o = np.broadcast_to(o, (nz, ny, nx))
+    return Primitive(st[o, 0], st[o, 1], st[o, 2], st[o, 4], None, st[o, 3])
+
+
+def smooth_wave_3d(nx: int, ny: int | None = None, nz: int | None = None, t: float = 0.0) -> Primitive:
+    """rho = 1 + 0.2 sin(2 pi (x + y + z - t)), u = v = w = 1/3, p = 1 (periodic
+    cube): the exact solution at time t is the initial profile moved by t/3
+    along each axis."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    x, y, z = _grid3(nx, ny, nz)
+    rho = 1.0 + 0.2 * np.sin(2.0 * math.pi * (x + y + z - t))
+    one = np.ones((nz, ny, nx))
+    return Primitive(rho * one, one / 3.0, one / 3.0, one.copy(), None, one / 3.0)
+
+
+def shear_layer_3d(nx: int, ny: int | None = None, nz: int | None = None, seed: int = 0,
+                   amplitude: float = 0.01, modes: int = 8) -> Primitive:
+    """The Kelvin-Helmholtz layer of kelvin_helmholtz (rho 2 / u +0.5 inside
+    |y - 0.5| < 0.25, rho 1 / u -0.5 outside, p 2.5) with the seeded
+    perturbation v = amplitude S(x) / max|S| of that function times
+    cos(2 pi z), and w = 0."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    kh = kelvin_helmholtz(nx, ny, seed=seed, amplitude=amplitude, modes=modes)
+    z = cell_centres(nz)[:, None, None]
+    one = np.ones((nz, ny, nx))
+    v = kh.v[None] * np.cos(2.0 * math.pi * z)
+    return Primitive(kh.rho[None] * one, kh.u[None] * one, v * one, kh.p[None] * one, None, np.zeros((nz, ny, nx)))

@@ -19,28 +19,31 @@ from oracle import oracle as O
 from paper_1607_08710_gb300 import inputs
 
 MUTANTS = {
-    "muscl_half_dropped": ("qL[l] = q_at(l, iL, j) + 0.5 * sL;", "qL[l] = q_at(l, iL, j) + sL;"),
+    "muscl_half_dropped": ("qL[l] = q_at(l, d, -1, i, j, k) + 0.5 * sL;", "qL[l] = q_at(l, d, -1, i, j, k) + sL;"),
     "pstar_jump_sign": ("- (rL * rR / rs) * a * (uR - uL);", "+ (rL * rR / rs) * a * (uR - uL);"),
     "ustar_pressure_sign": ("- (pR - pL) / (rs * a);", "- (pL - pR) / (rs * a);"),
     "upwind_flipped": ("(val(ustar) > 0.0) ? qL : qR;", "(val(ustar) > 0.0) ? qR : qL;"),
-    "y_slope_wrong_axis": ("S sL = limiter(c, q_at(l, i, jL) - q_at(l, i, jL - 1),",
-                           "S sL = limiter(c, q_at(l, i, jL) - q_at(l, i - 1, jL),"),
-    "energy_flux_no_pu": ("F[3] = F[3] + pstar * ustar;", "F[3] = F[3];"),
-    "heun_corrector_only": ("U[l][k] = U[l][k] - dt * ((bn + bs) / 2.0);", "U[l][k] = U[l][k] - dt * bs;"),
-    "eos_half_dropped": ("q[3] = (c.gamma - 1.0) * rho * (E - 0.5 * (u * u + v * v));",
-                         "q[3] = (c.gamma - 1.0) * rho * (E - (u * u + v * v));"),
+    "slope_on_wrong_axis": ("S sL = limiter(c, q_at(l, d, -1, i, j, k) - q_at(l, d, -2, i, j, k),",
+                            "S sL = limiter(c, q_at(l, d, -1, i, j, k) - q_at(l, 0, -2, i, j, k),"),
+    "energy_flux_no_pu": ("F[e] = F[e] + pstar * ustar;", "F[e] = F[e];"),
+    "heun_corrector_only": ("U[l][x] = U[l][x] - dt * ((bn + bs) / 2.0);", "U[l][x] = U[l][x] - dt * bs;"),
+    "eos_half_dropped": ("q[e] = (c.gamma - 1.0) * rho * (E - 0.5 * kin);", "q[e] = (c.gamma - 1.0) * rho * (E - kin);"),
     "sweby_beta_both": ("min_first(S(beta * aa), bb)", "min_first(S(beta * aa), S(beta * bb))"),
     "limiter_sign_lost": ("return val(a) > 0.0 ? m : S(-m);", "return m;"),
-    "y_balance_sign": ("Ay * north - Ay * south", "Ay * south - Ay * north"),
+    "balance_sign": ("acc = acc + A * ahead - A * behind;", "acc = acc + A * behind - A * ahead;"),
     "max_c_is_min": ("S a = max_first(cL, cR);", "S a = min_first(cL, cR);"),
-    "dt_without_y": ("if (c.dim == 2) s += (std::fabs(q[2]) + a) / c.dy;", ""),
+    "dt_speed_of_one_axis": ("s += (std::fabs(q[1 + d]) + a) / m.h[d];", "s += (std::fabs(q[1]) + a) / m.h[d];"),
     "momentum_pressure_wrong_axis": ("F[1 + dir] = F[1 + dir] + pstar;", "F[1] = F[1] + pstar;"),
-    "rk3_stage2_weight": ("U2[l][k] = 0.75 * U[l][k] + 0.25 *", "U2[l][k] = 0.70 * U[l][k] + 0.30 *"),
-    "species_fraction_not_divided": ("q[4 + k] = U[4 + k] / rho;", "q[4 + k] = U[4 + k];"),
-    "species_cons_without_rho": ("U[4 + k] = rho * q[4 + k];", "U[4 + k] = q[4 + k];"),
-    "species_fraction_of_wrong_species": ("q[4 + k] = U[4 + k] / rho;", "q[4 + k] = U[4 + c.nspecies - 1 - k] / rho;"),
-    "species_update_skips_last": ("for (int l = 0; l < nf; ++l) Us[l][k] = U[l][k] - dt",
-                                  "for (int l = 0; l < nf - (nf > 4); ++l) Us[l][k] = U[l][k] - dt"),
+    "rk3_stage2_weight": ("U2[l][x] = 0.75 * U[l][x] + 0.25 *", "U2[l][x] = 0.70 * U[l][x] + 0.30 *"),
+    "species_fraction_not_divided": ("q[e + 1 + k] = U[e + 1 + k] / rho;", "q[e + 1 + k] = U[e + 1 + k];"),
+    "species_cons_without_rho": ("U[e + 1 + k] = rho * q[e + 1 + k];", "U[e + 1 + k] = q[e + 1 + k];"),
+    "species_fraction_of_wrong_species": ("q[e + 1 + k] = U[e + 1 + k] / rho;",
+                                          "q[e + 1 + k] = U[e + c.nspecies - k] / rho;"),
+    "species_update_skips_last": ("for (int l = 0; l < nf; ++l) Us[l][x] = U[l][x] - dt",
+                                  "for (int l = 0; l < nf - (c.nspecies > 0); ++l) Us[l][x] = U[l][x] - dt"),
+    "w_missing_from_eos": ("kin = kin + q[1 + d] * q[1 + d];", "kin = kin + (d < 2 ? q[1 + d] * q[1 + d] : S(0.0));"),
+    "face_area_one_factor": ("const double A = m.h[(d + 1) % 3] * m.h[(d + 2) % 3];",
+                             "const double A = m.h[(d + 1) % 3];"),
 }
 
 
@@ -152,6 +155,42 @@ def battery():
         except O.OracleError:
             es.append(np.inf)
     check("species_order2", np.all(np.isfinite(es)) and es[1] > 0 and math.log2(es[0] / es[1]) > 1.75)
+    # 3D: a z-only tube equals the 1D scheme; an axis permutation commutes
+    # with the step; the 3D CFL dt by hand
+    n = 24
+    tube = inputs.named_shock_tube("sod", n).stack()[:, 0, :]
+    c1 = O.OracleConfig(nx=n, dim=1, limiter="minmod")
+    dts3 = [3e-3] * 6
+    try:
+        r1 = O.run(c1, O.prim_to_cons(c1, tube[:, None, :]), 6, dts=dts3, allow_nonphysical=True).U[:, 0, :]
+        q3 = np.zeros((5, n, 1, 1))
+        q3[0, :, 0, 0], q3[3, :, 0, 0], q3[4, :, 0, 0] = tube[0], tube[1], tube[3]
+        cz = O.OracleConfig(nx=1, ny=1, nz=n, dim=3, limiter="minmod")
+        rz = O.run(cz, O.prim_to_cons(cz, q3), 6, dts=dts3, allow_nonphysical=True).U.reshape(5, n)
+        check("z_tube_is_1d", np.allclose(rz[[0, 3, 4]], r1[[0, 1, 3]], rtol=1e-13, atol=1e-14))
+    except O.OracleError:
+        check("z_tube_is_1d", False)
+    qo = inputs.octant(5, 4, 3, seed=1).stack()
+    co = O.OracleConfig(nx=5, ny=4, nz=3, dim=3, lx=1.0, ly=1.3, lz=0.7)
+    cp = O.OracleConfig(nx=3, ny=5, nz=4, dim=3, lx=0.7, ly=1.0, lz=1.3)
+    perm = [2, 0, 1]  # new axis d = old axis perm[d]
+
+    def relabel(U):
+        order = [0] + [1 + (2 - perm[2 - p]) for p in range(3)]
+        out = np.transpose(U, order).copy()
+        for d in range(3):
+            out[1 + d] = np.transpose(U[1 + perm[d]], [2 - perm[2 - p] for p in range(3)])
+        return np.ascontiguousarray(out)
+    try:
+        ro = O.run(co, O.prim_to_cons(co, qo), 3, dts=[2e-3] * 3, allow_nonphysical=True).U
+        rp = O.run(cp, O.prim_to_cons(cp, relabel(qo)), 3, dts=[2e-3] * 3, allow_nonphysical=True).U
+        check("permute_3d", np.allclose(rp, relabel(ro), rtol=1e-12, atol=1e-13))
+    except O.OracleError:
+        check("permute_3d", False)
+    one = np.ones((5, 8, 10))
+    qd = np.stack([1.4 * one, 0.5 * one, -0.25 * one, 0.1 * one, one])
+    cd3 = O.OracleConfig(nx=10, ny=8, nz=5, dim=3, cfl=0.45)
+    check("dt_hand_3d", math.isclose(O.cfl_dt(cd3, O.prim_to_cons(cd3, qd)), 0.45 / (15 + 10 + 5.5), rel_tol=1e-12))
     return fails
 
 
