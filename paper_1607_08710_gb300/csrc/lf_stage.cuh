@@ -7,7 +7,8 @@
 // and upwinded with the gas state, so they add planes, not passes.
 //
 // Work decomposition.  A warp owns a strip of 32*CPL consecutive columns,
-// CPL cells per lane.  The two columns at each end are the halo the 5-point
+// CPL cells per lane, computed as one lane value (FP32: both cells of a lane
+// as a packed pair on the paired FP32 instructions; FP64: one cell).  The two columns at each end are the halo the 5-point
 // MUSCL stencil needs, so a strip produces 32*CPL - 4 output columns and all
 // x-neighbour exchange is done with warp shuffles (no shared memory, no
 // __syncthreads).  The warp marches up a tile of rows carrying the y-stencil
@@ -127,60 +128,61 @@ __device__ __forceinline__ LaneCols<CPL> lane_cols(int i0, int lane, int nx, int
   return L;
 }
 
+// A lane value from / to the CPL cells of a lane.
+__device__ __forceinline__ void make_lane(const float v[1], float& out) { out = v[0]; }
+__device__ __forceinline__ void make_lane(const double v[1], double& out) { out = v[0]; }
+__device__ __forceinline__ void make_lane(const float v[2], F2& out) { out = F2(v[0], v[1]); }
+__device__ __forceinline__ void split_lane(float x, float v[1]) { v[0] = x; }
+__device__ __forceinline__ void split_lane(double x, double v[1]) { v[0] = x; }
+__device__ __forceinline__ void split_lane(F2 x, float v[2]) {
+  v[0] = x.v.x;
+  v[1] = x.v.y;
+}
+
+// The values one cell to the left / right of each of the lane's cells (the
+// neighbouring lane's cells by warp shuffle).
+constexpr unsigned FULL_MASK = 0xffffffffu;
+__device__ __forceinline__ float prev_cell(float q) { return __shfl_up_sync(FULL_MASK, q, 1); }
+__device__ __forceinline__ double prev_cell(double q) { return __shfl_up_sync(FULL_MASK, q, 1); }
+__device__ __forceinline__ F2 prev_cell(F2 q) { return F2(__shfl_up_sync(FULL_MASK, q.v.y, 1), q.v.x); }
+__device__ __forceinline__ float next_cell(float q) { return __shfl_down_sync(FULL_MASK, q, 1); }
+__device__ __forceinline__ double next_cell(double q) { return __shfl_down_sync(FULL_MASK, q, 1); }
+__device__ __forceinline__ F2 next_cell(F2 q) { return F2(q.v.y, __shfl_down_sync(FULL_MASK, q.v.x, 1)); }
+
 // Conservative values of this lane's CPL cells in row `off` (= mapped row * pitch).
-template <typename T, int CPL, int NF>
+template <typename T, int CPL, int NF, typename V>
 __device__ __forceinline__ void load_row(const T* const __restrict__ P[NF], const LaneCols<CPL>& L, int off,
-                                         T U[CPL][NF]) {
-  if (L.vec_ok) {
+                                         V U[NF]) {
 #pragma unroll
-    for (int k = 0; k < NF; ++k) {
-      T v[CPL];
+  for (int k = 0; k < NF; ++k) {
+    T v[CPL];
+    if (L.vec_ok) {
       VecLoad<T, CPL>::load(P[k] + off + L.c0, v);
+    } else {
 #pragma unroll
-      for (int j = 0; j < CPL; ++j) U[j][k] = v[j];
+      for (int j = 0; j < CPL; ++j) v[j] = __ldg(P[k] + off + L.ic[j]);
     }
-  } else {
-#pragma unroll
-    for (int k = 0; k < NF; ++k)
-#pragma unroll
-      for (int j = 0; j < CPL; ++j) U[j][k] = __ldg(P[k] + off + L.ic[j]);
+    make_lane(v, U[k]);
   }
 }
 
-// Fluxes through the x-faces of this lane's cells, from the primitive states
-// q of the lane's CPL columns in the current row.  Fl[j] / Fr[j]: left and
-// right face of cell j (valid for output cells).
-template <typename T, int LIM, int CPL, int NF>
-__device__ __forceinline__ void x_fluxes(const Phys<T>& P, const T q[CPL][NF], T Fl[CPL][NF], T Fr[CPL][NF]) {
-  constexpr unsigned FULL = 0xffffffffu;
-  T qL[CPL][NF], qR[CPL][NF];  // qL[j]: left state of face j+1/2; qR[j]: right state of face j-1/2
+// Fluxes through the x-faces of this lane's cells, from the primitive lane
+// values q of the current row.  Fr: right face of each cell, Fl: left face
+// (valid for output cells).  Every x-face of the strip is computed once: the
+// faces to the right of the lane's cells, whose right states are the next
+// cells' (the last one from the next lane).
+template <typename V, int LIM, int NF>
+__device__ __forceinline__ void x_fluxes(const Phys<V>& P, const V q[NF], V Fl[NF], V Fr[NF]) {
+  V qL[NF], qR[NF];  // left and right states of each cell's right face
 #pragma unroll
   for (int k = 0; k < NF; ++k) {
-    const T left = __shfl_up_sync(FULL, q[CPL - 1][k], 1);  // column c0-1
-    const T right = __shfl_down_sync(FULL, q[0][k], 1);     // column c0+CPL
-    T dminus = q[0][k] - left;
-#pragma unroll
-    for (int j = 0; j < CPL; ++j) {
-      const T dplus = (j + 1 < CPL ? q[j + 1][k] : right) - q[j][k];
-      const T h = limiter_half<T, LIM>(dminus, dplus, P.beta);
-      qL[j][k] = q[j][k] + h;
-      qR[j][k] = q[j][k] - h;
-      dminus = dplus;
-    }
+    const V h = limiter_half<V, LIM>(q[k] - prev_cell(q[k]), next_cell(q[k]) - q[k], P.beta);
+    qL[k] = q[k] + h;
+    qR[k] = next_cell(q[k] - h);
   }
-  // internal faces j+1/2 for j < CPL-1, then the face shared with the next lane
+  lagrange_flux<V, 0, NF>(P, qL, qR, Fr);
 #pragma unroll
-  for (int j = 0; j + 1 < CPL; ++j) {
-    lagrange_flux<T, 0, NF>(P, qL[j], qR[j + 1], Fr[j]);
-#pragma unroll
-    for (int k = 0; k < NF; ++k) Fl[j + 1][k] = Fr[j][k];
-  }
-  T qRnext[NF];
-#pragma unroll
-  for (int k = 0; k < NF; ++k) qRnext[k] = __shfl_down_sync(FULL, qR[0][k], 1);
-  lagrange_flux<T, 0, NF>(P, qL[CPL - 1], qRnext, Fr[CPL - 1]);
-#pragma unroll
-  for (int k = 0; k < NF; ++k) Fl[0][k] = __shfl_up_sync(FULL, Fr[CPL - 1][k], 1);
+  for (int k = 0; k < NF; ++k) Fl[k] = prev_cell(Fr[k]);
 }
 
 // Warp-level max and any(), then one atomic per warp.
@@ -196,10 +198,11 @@ __device__ __forceinline__ void publish_speed(Scalars* sc, int wpar, T smax, boo
   }
 }
 
-// Cells per lane and tile height per precision (FP64 keeps one cell per lane
-// to stay clear of register spills).
-template <typename T> struct StageShape { static constexpr int CPL = 2, TY = LF_TY_F32; };
-template <> struct StageShape<double> { static constexpr int CPL = 1, TY = LF_TY_F64; };
+// Cells per lane, lane value and tile height per precision (FP32: two cells
+// per lane as one packed pair; FP64 keeps one cell per lane to stay clear of
+// register spills).
+template <typename T> struct StageShape { static constexpr int CPL = 2, TY = LF_TY_F32; using V = F2; };
+template <> struct StageShape<double> { static constexpr int CPL = 1, TY = LF_TY_F64; using V = double; };
 
 // ---------------------------------------------------------------------------
 // Asynchronous row staging.  Every row a warp reads from global memory is
@@ -266,14 +269,13 @@ __device__ __forceinline__ void issue_out_cells(T* buf, const T* const P[NF], co
   }
 }
 
-template <typename T, int CPL, int NF>
-__device__ __forceinline__ void read_row(const T* buf, int lane, T V[CPL][NF]) {
+template <typename T, int CPL, int NF, typename V>
+__device__ __forceinline__ void read_row(const T* buf, int lane, V out[NF]) {
 #pragma unroll
   for (int k = 0; k < NF; ++k) {
     T v[CPL];
     VecLoad<T, CPL>::load_plain(buf + (k * 32 + lane) * CPL, v);
-#pragma unroll
-    for (int j = 0; j < CPL; ++j) V[j][k] = v[j];
+    make_lane(v, out[k]);
   }
 }
 
@@ -291,10 +293,10 @@ template <> struct StageCoef<2> { static constexpr double alpha = 0.75, beta = 0
 template <> struct StageCoef<3> { static constexpr double alpha = 1.0 / 3.0, beta = 2.0 / 3.0; static constexpr bool speed = true; };
 
 // State of the y-march: three register slots indexed by row mod 3.
-template <typename T, int CPL, int NF> struct March {
-  T q[3][CPL][NF];  // primitives of rows r, r+1, r+2
-  T s[3][CPL][NF];  // half y-slopes (limiter_half)
-  T G[3][CPL][NF];  // G[slot(r)] = flux through face r-1/2
+template <typename V, int NF> struct March {
+  V q[3][NF];  // primitives of rows r, r+1, r+2
+  V s[3][NF];  // half y-slopes (limiter_half)
+  V G[3][NF];  // G[slot(r)] = flux through face r-1/2
 };
 
 template <typename T, int STAGE, int CPL, int NF> struct StageArgs {
@@ -315,10 +317,10 @@ __device__ __forceinline__ int ring_in_plus(int si, int k) {
   return t >= RING_IN ? t - RING_IN : t;
 }
 
-template <typename T, int LIM, int STAGE, int CPL, int NF, int S>
-__device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m,
+template <typename T, typename V, int LIM, int STAGE, int CPL, int NF, int S>
+__device__ __forceinline__ void march_row(const Phys<V>& P, const MeshDesc& m,
                                           const StageArgs<T, STAGE, CPL, NF>& A, const LaneCols<CPL>& L,
-                                          March<T, CPL, NF>& M, int lane, int r, int si, int jend, T cx, T cy,
+                                          March<V, NF>& M, int lane, int r, int si, int jend, V ncx, V ncy,
                                           T& smax, bool& bad) {
   constexpr int S1 = (S + 1) % 3, S2 = (S + 2) % 3;
   constexpr int ROW = Ring<T, CPL, NF>::ROW;
@@ -326,10 +328,9 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m,
   // the group issued two rows ago (input row r+2, U^n row r) has landed
   cp_wait<1>();
   {
-    T Ut[CPL][NF];
+    V Ut[NF];
     read_row<T, CPL, NF>(A.ring_in + ring_in_plus(si, 2) * ROW, lane, Ut);
-#pragma unroll
-    for (int j = 0; j < CPL; ++j) to_prim<T, NF>(P, Ut[j], M.q[S2][j]);
+    to_prim<V, NF>(P, Ut, M.q[S2]);
   }
   // Rows r+4 (input) and r+2 (U^n) are issued on every row, also near the
   // end of the tile where they are not needed: the row index stays valid
@@ -342,42 +343,38 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m,
     issue_out_cells<T, CPL, NF>(A.ring_un + S2 * ROW, A.N, L, min(r + AHEAD_UN, m.ny - 1) * m.pitch, lane);
   cp_commit();
   // y-slopes of row r+1 and the flux through face r+1/2
-#pragma unroll
-  for (int j = 0; j < CPL; ++j) {
-    T Lq[NF], Rq[NF];
+  {
+    V Lq[NF], Rq[NF];
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
-      M.s[S1][j][k] = limiter_half<T, LIM>(M.q[S1][j][k] - M.q[S][j][k], M.q[S2][j][k] - M.q[S1][j][k], P.beta);
-      Lq[k] = M.q[S][j][k] + M.s[S][j][k];
-      Rq[k] = M.q[S1][j][k] - M.s[S1][j][k];
+      M.s[S1][k] = limiter_half<V, LIM>(M.q[S1][k] - M.q[S][k], M.q[S2][k] - M.q[S1][k], P.beta);
+      Lq[k] = M.q[S][k] + M.s[S][k];
+      Rq[k] = M.q[S1][k] - M.s[S1][k];
     }
-    lagrange_flux<T, 1, NF>(P, Lq, Rq, M.G[S1][j]);
+    lagrange_flux<V, 1, NF>(P, Lq, Rq, M.G[S1]);
   }
   // x-faces of row r
-  T Fl[CPL][NF], Fr[CPL][NF];
-  x_fluxes<T, LIM, CPL, NF>(P, M.q[S], Fl, Fr);
+  V Fl[NF], Fr[NF];
+  x_fluxes<V, LIM, NF>(P, M.q[S], Fl, Fr);
   // update the output cells of row r (computed on every lane; only output
   // cells are stored and enter the wave-speed maximum)
-  T U[CPL][NF], Un[CPL][NF];
+  V U[NF], Un[NF];
   read_row<T, CPL, NF>(A.ring_in + si * ROW, lane, U);
   if (STAGE >= 1) read_row<T, CPL, NF>(A.ring_un + S * ROW, lane, Un);
-  T W[CPL][NF];
+  V W[NF];
 #pragma unroll
-  for (int j = 0; j < CPL; ++j)
-#pragma unroll
-    for (int k = 0; k < NF; ++k) {
-      const T base = STAGE == 0 ? U[j][k]
-                    : STAGE == 1 ? T(0.5) * (Un[j][k] + U[j][k])
-                                 : fma_(T(StageCoef<STAGE>::alpha), Un[j][k], T(StageCoef<STAGE>::beta) * U[j][k]);
-      W[j][k] = fma_(-cy, M.G[S1][j][k] - M.G[S][j][k], fma_(-cx, Fr[j][k] - Fl[j][k], base));
-    }
+  for (int k = 0; k < NF; ++k) {
+    const V base = STAGE == 0 ? U[k]
+                 : STAGE == 1 ? splat<V>(0.5) * (Un[k] + U[k])
+                              : fma_(splat<V>(StageCoef<STAGE>::alpha), Un[k], splat<V>(StageCoef<STAGE>::beta) * U[k]);
+    W[k] = fma_(ncy, M.G[S1][k] - M.G[S][k], fma_(ncx, Fr[k] - Fl[k], base));
+  }
   const int off = r * m.pitch;
   if (L.vec_ok && L.any_out) {
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
       T v[CPL];
-#pragma unroll
-      for (int j = 0; j < CPL; ++j) v[j] = W[j][k];
+      split_lane(W[k], v);
       VecLoad<T, CPL>::store(A.O[k] + off + L.c0, v);
     }
   } else if (!L.vec_ok) {
@@ -385,15 +382,15 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m,
     for (int j = 0; j < CPL; ++j)
       if (L.out[j])
 #pragma unroll
-        for (int k = 0; k < NF; ++k) A.O[k][off + L.c0 + j] = W[j][k];
+        for (int k = 0; k < NF; ++k) A.O[k][off + L.c0 + j] = get(W[k], j);
   }
   if (StageCoef<STAGE>::speed) {
+    typename LaneT<V>::M ok;
+    const V sp = cell_speed<V, 2>(P, W, ok);
 #pragma unroll
     for (int j = 0; j < CPL; ++j) {
-      bool ok;
-      const T sp = cell_speed<T, 2>(P, W[j], ok);
-      smax = L.out[j] ? fmax(smax, sp) : smax;
-      bad |= L.out[j] && !ok;
+      smax = L.out[j] ? fmax(smax, get(sp, j)) : smax;
+      bad |= L.out[j] && !get(ok, j);
     }
   }
 }
@@ -402,8 +399,8 @@ __device__ __forceinline__ void march_row(const Phys<T>& P, const MeshDesc& m,
 // [j0, jend): the whole y-march, from the prologue to the last row.  The
 // warp's rings start empty and are left with no copy in flight.
 // STAGE 0: out = Uin - dt L(Uin).  STAGE 1: out = (Un + Uin)/2 - dt/2 L(Uin).
-template <typename T, int LIM, int STAGE, int CPL, int NF>
-__device__ __forceinline__ void strip_tile(const Phys<T>& P, const MeshDesc& m, const T* Uin, const T* Un, T* out,
+template <typename T, typename V, int LIM, int STAGE, int CPL, int NF>
+__device__ __forceinline__ void strip_tile(const Phys<V>& P, const MeshDesc& m, const T* Uin, const T* Un, T* out,
                                            int i0, int j0, int jend, T cx, T cy, T* ring_in, int lane, T& smax,
                                            bool& bad) {
   const LaneCols<CPL> L = lane_cols<CPL>(i0, lane, m.nx, m.bc, m.vec);
@@ -433,29 +430,25 @@ __device__ __forceinline__ void strip_tile(const Phys<T>& P, const MeshDesc& m, 
   if (STAGE >= 1 && L.any_out) issue_out_cells<T, CPL, NF>(A.ring_un + 0 * ROW, A.N, L, j0 * m.pitch, lane);
   cp_commit();
   cp_wait<1>();
-  March<T, CPL, NF> M;
+  March<V, NF> M;
   {
-    T Ut[CPL][NF];
+    V Ut[NF];
     const int slot_of[4] = {1, 2, 0, 1};  // rows j0-2, j0-1, j0, j0+1 -> register slots
-    T qm2[CPL][NF];
+    V qm2[NF];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       read_row<T, CPL, NF>(A.ring_in + ring_slot(j0 - 2 + t, j0, RING_IN) * ROW, lane, Ut);
-#pragma unroll
-      for (int j = 0; j < CPL; ++j) to_prim<T, NF>(P, Ut[j], t == 0 ? qm2[j] : M.q[slot_of[t]][j]);
+      to_prim<V, NF>(P, Ut, t == 0 ? qm2 : M.q[slot_of[t]]);
     }
+    V Lq[NF], Rq[NF];
 #pragma unroll
-    for (int j = 0; j < CPL; ++j) {
-      T Lq[NF], Rq[NF];
-#pragma unroll
-      for (int k = 0; k < NF; ++k) {
-        M.s[2][j][k] = limiter_half<T, LIM>(M.q[2][j][k] - qm2[j][k], M.q[0][j][k] - M.q[2][j][k], P.beta);
-        M.s[0][j][k] = limiter_half<T, LIM>(M.q[0][j][k] - M.q[2][j][k], M.q[1][j][k] - M.q[0][j][k], P.beta);
-        Lq[k] = M.q[2][j][k] + M.s[2][j][k];
-        Rq[k] = M.q[0][j][k] - M.s[0][j][k];
-      }
-      lagrange_flux<T, 1, NF>(P, Lq, Rq, M.G[0][j]);
+    for (int k = 0; k < NF; ++k) {
+      M.s[2][k] = limiter_half<V, LIM>(M.q[2][k] - qm2[k], M.q[0][k] - M.q[2][k], P.beta);
+      M.s[0][k] = limiter_half<V, LIM>(M.q[0][k] - M.q[2][k], M.q[1][k] - M.q[0][k], P.beta);
+      Lq[k] = M.q[2][k] + M.s[2][k];
+      Rq[k] = M.q[0][k] - M.s[0][k];
     }
+    lagrange_flux<V, 1, NF>(P, Lq, Rq, M.G[0]);
   }
   if (j0 + 1 < jend) {
     issue_row<T, CPL, NF>(A.ring_in + ring_slot(j0 + 3, j0, RING_IN) * ROW, A.P, L,
@@ -465,15 +458,17 @@ __device__ __forceinline__ void strip_tile(const Phys<T>& P, const MeshDesc& m, 
   }
   cp_commit();
 
-  // si: input-ring slot of row r (row j0 is in slot 0)
+  // si: input-ring slot of row r (row j0 is in slot 0); the update's dt/dx
+  // and dt/dy enter negated (fma(-c, d, b) == fma(c', d, b) with c' = -c)
+  const V ncx = V(-cx), ncy = V(-cy);
   for (int r = j0, si = 0;;) {
-    march_row<T, LIM, STAGE, CPL, NF, 0>(P, m, A, L, M, lane, r, si, jend, cx, cy, smax, bad);
+    march_row<T, V, LIM, STAGE, CPL, NF, 0>(P, m, A, L, M, lane, r, si, jend, ncx, ncy, smax, bad);
     if (++r >= jend) break;
     si = ring_in_plus(si, 1);
-    march_row<T, LIM, STAGE, CPL, NF, 1>(P, m, A, L, M, lane, r, si, jend, cx, cy, smax, bad);
+    march_row<T, V, LIM, STAGE, CPL, NF, 1>(P, m, A, L, M, lane, r, si, jend, ncx, ncy, smax, bad);
     if (++r >= jend) break;
     si = ring_in_plus(si, 1);
-    march_row<T, LIM, STAGE, CPL, NF, 2>(P, m, A, L, M, lane, r, si, jend, cx, cy, smax, bad);
+    march_row<T, V, LIM, STAGE, CPL, NF, 2>(P, m, A, L, M, lane, r, si, jend, ncx, ncy, smax, bad);
     if (++r >= jend) break;
     si = ring_in_plus(si, 1);
   }
@@ -506,7 +501,8 @@ stage2d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
   const double dtd = sc->dt;
   if (!(dtd > 0.0)) return;
   const int wpar = sc->parity ^ 1;
-  const Phys<T> P(m);
+  using V = typename StageShape<T>::V;
+  const Phys<V> P(m);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i0 = (blockIdx.x * STAGE_WARPS + warp) * StripGeom<CPL>::OUT;
   if (i0 >= m.nx) return;  // whole warp
@@ -517,7 +513,7 @@ stage2d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
   T* ring = reinterpret_cast<T*>(lf_stage_smem + warp * Ring<T, CPL, NF>::warp_bytes(STAGE));
   T smax = T(0);
   bool bad = false;
-  strip_tile<T, LIM, STAGE, CPL, NF>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring, lane, smax, bad);
+  strip_tile<T, V, LIM, STAGE, CPL, NF>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring, lane, smax, bad);
   if (StageCoef<STAGE>::speed) publish_speed(sc, wpar, smax, bad);
 }
 
@@ -555,13 +551,14 @@ batch_stage_kernel(const BatchDesc b, const T* Uin, const T* Un, T* out, Scalars
     m.plane = pd.plane;
     m.rdx = pd.rdx;
     m.rdy = pd.rdy;
-    const Phys<T> P(m);
+    using V = typename StageShape<T>::V;
+    const Phys<V> P(m);
     const double hs = StageCoef<STAGE>::beta;
     const T cx = T(hs * dtd * m.rdx), cy = T(hs * dtd * m.rdy);
     T smax = T(0);
     bool bad = false;
-    strip_tile<T, LIM, STAGE, CPL, 4>(P, m, Uin + pd.off, Un + pd.off, out + pd.off, un.i0, un.j0, un.jend, cx, cy,
-                                      ring, lane, smax, bad);
+    strip_tile<T, V, LIM, STAGE, CPL, 4>(P, m, Uin + pd.off, Un + pd.off, out + pd.off, un.i0, un.j0, un.jend, cx,
+                                         cy, ring, lane, smax, bad);
     if (StageCoef<STAGE>::speed) publish_speed(scp, scp->parity ^ 1, smax, bad);
   }
 }
@@ -591,43 +588,51 @@ int batch_blocks_lim(int stage) {
 template <typename T, int LIM, int STAGE, int CPL, int NF>
 __global__ void __launch_bounds__(STAGE_WARPS * 32)
 stage1d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out, Scalars* sc) {
+  using V = typename StageShape<T>::V;
   const double dtd = sc->dt;
   if (!(dtd > 0.0)) return;
   const int wpar = sc->parity ^ 1;
-  const Phys<T> P(m);
+  const Phys<V> P(m);
   const int lane = threadIdx.x & 31;
   const int i0 = (blockIdx.x * STAGE_WARPS + (threadIdx.x >> 5)) * StripGeom<CPL>::OUT;
   if (i0 >= m.nx) return;
   const LaneCols<CPL> L = lane_cols<CPL>(i0, lane, m.nx, m.bc, m.vec);
-  const T cx = T(StageCoef<STAGE>::beta * dtd * m.rdx);
+  const V ncx = V(-T(StageCoef<STAGE>::beta * dtd * m.rdx));
   const T* Pp[NF];
 #pragma unroll
   for (int k = 0; k < NF; ++k) Pp[k] = Uin + k * m.plane;
-  T U[CPL][NF], q[CPL][NF], Fl[CPL][NF], Fr[CPL][NF];
+  V U[NF], q[NF], Fl[NF], Fr[NF];
   load_row<T, CPL, NF>(Pp, L, 0, U);
+  to_prim<V, NF>(P, U, q);
+  x_fluxes<V, LIM, NF>(P, q, Fl, Fr);
+  V W[NF];
 #pragma unroll
-  for (int j = 0; j < CPL; ++j) to_prim<T, NF>(P, U[j], q[j]);
-  x_fluxes<T, LIM, CPL, NF>(P, q, Fl, Fr);
+  for (int k = 0; k < NF; ++k) {
+    V base = U[k];
+    if (STAGE >= 1) {
+      T v[CPL];  // U^n at the lane's output cells (other cells: any finite value, never stored)
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) v[j] = L.out[j] ? Un[k * m.plane + L.c0 + j] : T(0);
+      V un;
+      make_lane(v, un);
+      base = STAGE == 1 ? splat<V>(0.5) * (un + U[k])
+                        : fma_(splat<V>(StageCoef<STAGE>::alpha), un, splat<V>(StageCoef<STAGE>::beta) * U[k]);
+    }
+    W[k] = fma_(ncx, Fr[k] - Fl[k], base);
+  }
   T smax = T(0);
   bool bad = false;
+  typename LaneT<V>::M ok;
+  V sp;
+  if (StageCoef<STAGE>::speed) sp = cell_speed<V, 1>(P, W, ok);
 #pragma unroll
   for (int j = 0; j < CPL; ++j) {
     if (!L.out[j]) continue;
-    const int c = L.c0 + j;
-    T W[NF];
 #pragma unroll
-    for (int k = 0; k < NF; ++k) {
-      const T base = STAGE == 0 ? U[j][k]
-                    : STAGE == 1 ? T(0.5) * (Un[k * m.plane + c] + U[j][k])
-                                 : fma_(T(StageCoef<STAGE>::alpha), Un[k * m.plane + c], T(StageCoef<STAGE>::beta) * U[j][k]);
-      W[k] = fma_(-cx, Fr[j][k] - Fl[j][k], base);
-    }
-#pragma unroll
-    for (int k = 0; k < NF; ++k) out[k * m.plane + c] = W[k];
+    for (int k = 0; k < NF; ++k) out[k * m.plane + L.c0 + j] = get(W[k], j);
     if (StageCoef<STAGE>::speed) {
-      bool ok;
-      smax = fmax(smax, cell_speed<T, 1>(P, W, ok));
-      bad |= !ok;
+      smax = fmax(smax, get(sp, j));
+      bad |= !get(ok, j);
     }
   }
   if (StageCoef<STAGE>::speed) publish_speed(sc, wpar, smax, bad);
