@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--rk3-steps", type=int, default=100)
     ap.add_argument("--no-species", action="store_true")
     ap.add_argument("--species-steps", type=int, default=100)
+    ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--size3d", type=int, default=384)
+    ap.add_argument("--steps3d", type=int, default=50)
     ap.add_argument("--batch-problems", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=300)
     return ap.parse_args()
@@ -481,6 +484,48 @@ def run_ours(args, dist):
                          "peak_kind": f"{peak_kind} copy bandwidth",
                          "algorithmic_bytes_per_cell": byts[sk] // cells},
             "workload": f"periodic shear layer {n}x{n} with tracers y_1 = layer indicator, y_2 = 1 - y_1"}
+        torch.cuda.empty_cache()
+
+    # the 3D step (faces normal to x, y and z) on a periodic 3D shear layer
+    if not args.no_3d and dist.rank == 0:
+        n3 = args.size3d
+        cells3 = n3 ** 3
+        s3d = LagrangeFlux(Config(nx=n3, ny=n3, nz=n3, dim=3, precision=prec, limiter="vanleer", bc="periodic",
+                                  cfl=0.45, device=dist.local_rank))
+        q = torch.from_numpy(inputs.shear_layer_3d(n3, seed=0).stack()).to(dev, tdt)
+        s3d.set_primitives(q)
+        del q
+        for _ in range(args.warmup):
+            s3d.step()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps3d):
+            s3d.step()
+        e1.record()
+        torch.cuda.synchronize()
+        t3d = e0.elapsed_time(e1) / 1e3
+        s3d.sync()
+        s3d.profile(True)
+        for _ in range(args.profile_steps):
+            s3d.step()
+        (a0, a1), (c0, c1) = s3d.profile_read()
+        s3d.close()
+        word = 4 if prec == "fp32" else 8
+        ms = {"stage0": a0 / c0, "stage1": a1 / c1}
+        byts = {"stage0": 2 * 5 * word * cells3, "stage1": 3 * 5 * word * cells3}
+        peak, peak_kind = peaks()
+        sk = max(ms, key=ms.get)
+        gbs = byts[sk] / (ms[sk] / 1e3) / 1e9
+        out["3d"] = {
+            "value": cells3 * args.steps3d / t3d, "unit": METRIC, "steps": args.steps3d,
+            "ms_per_step": 1e3 * t3d / args.steps3d, "stage_ms": [ms["stage0"], ms["stage1"]],
+            "roofline": {"bound": "hbm", "kernel": f"stage3d_kernel<{'float' if prec == 'fp32' else 'double'}, "
+                         f"VANLEER, {'predictor' if sk == 'stage0' else 'corrector'}>",
+                         "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "peak_kind": f"{peak_kind} copy bandwidth",
+                         "algorithmic_bytes_per_cell": byts[sk] // cells3},
+            "workload": f"periodic 3D shear layer {n3}^3 (Kelvin-Helmholtz layer, perturbation x cos(2 pi z))"}
         torch.cuda.empty_cache()
 
     # batched: 512 seeded uneven meshes, one persistent launch per stage, graph of the step loop

@@ -1,7 +1,7 @@
 /*
  * lagflux.h -- C ABI of the GB300 (sm_103a) Lagrange-flux solver.
  *
- * The library advances the 1D/2D compressible Euler equations with a
+ * The library advances the 1D/2D/3D compressible Euler equations with a
  * perfect-gas equation of state (arXiv:1607.08710, Sec. 3, eq. 1) by the
  * second-order Lagrange-flux scheme of Sec. 4: MUSCL reconstruction of the
  * primitive variables with a limited slope (eq. "sweby"), the Lagrangian
@@ -13,14 +13,20 @@
  * the gas state by the same Lagrange flux.
  *
  * Conventions shared by every entry point:
- *   - Mesh: a uniform Cartesian mesh of nx x ny cells on
- *     [xmin, xmax] x [ymin, ymax] (ny == 1 and the y bounds unused in 1D).
+ *   - Mesh: a uniform Cartesian mesh of nx x ny (x nz) cells on
+ *     [xmin, xmax] x [ymin, ymax] (x [zmin, zmax]); ny == 1 in 1D, nz == 1
+ *     (or 0) below 3D.  3D applies the same face formulas on a third axis
+ *     (the finite-volume form of Sec. 4 holds for any cell shape).
  *   - Fields are passed as separate planes of nx*ny elements, x fastest
  *     (element (i, j) at index j*nx + i), of the configured precision:
  *     double for LF_FP64, float for LF_FP32.  The conservative planes are
  *     (rho, rho u, rho v, rho E); the primitive planes (rho, u, v, p).
  *     Species planes (nspecies > 0) are passed as one buffer of nspecies
  *     consecutive planes: partial densities rho y_k or mass fractions y_k.
+ *     The whole-state calls (lf_set_conservative and friends) take one
+ *     buffer of all nfields planes: (rho, rho u, rho v, [rho w,] rho E,
+ *     rho y_k) or (rho, u, v, [w,] p, y_k), nfields = 4 (5 in 3D) + nspecies,
+ *     each plane nx*ny*nz values, x fastest, then y, then z.
  *   - Ownership: the caller owns every buffer it passes and keeps it; the
  *     library copies in and out and never retains a caller pointer.  The
  *     context owns its device state, scratch and scalars.
@@ -83,7 +89,7 @@ enum { LF_TIME_HEUN = 2, LF_TIME_SSPRK3 = 3 };
 #define LF_MAX_SPECIES 2
 
 typedef struct lf_config {
-  int32_t dim;       /* 1 or 2 */
+  int32_t dim;       /* 1, 2 or 3 */
   int32_t nx, ny;    /* cells per direction; ny == 1 when dim == 1 */
   int32_t limiter;   /* LF_LIMITER_* */
   int32_t bc;        /* LF_BC_* */
@@ -92,13 +98,16 @@ typedef struct lf_config {
   int32_t device;    /* CUDA device ordinal */
   int32_t time_order; /* LF_TIME_* (0 = LF_TIME_HEUN) */
   int32_t nspecies;  /* transported mass fractions, 0 .. LF_MAX_SPECIES (Sec. 5);
-                        lf_init contexts only (0 for batches, the adjoint and
-                        lf_step_noalloc) */
+                        lf_init contexts of dim 1 or 2 only (0 for 3D,
+                        batches, the adjoint and lf_step_noalloc) */
   double xmin, xmax; /* domain in x */
   double ymin, ymax; /* domain in y (ignored in 1D) */
   double gamma;      /* ratio of specific heats, 1 < gamma <= 3 (Sec. 3) */
   double cfl;        /* CFL number, 0 < cfl <= 1 */
   double beta;       /* Sweby coefficient, 1 <= beta <= 2 (LF_LIMITER_SWEBY) */
+  int32_t nz;        /* cells in z (dim == 3); 0 or 1 otherwise */
+  int32_t reserved;  /* must be 0 */
+  double zmin, zmax; /* domain in z (dim == 3) */
 } lf_config;
 
 typedef struct lf_ctx lf_ctx;
@@ -130,6 +139,17 @@ lf_status lf_get_state(lf_ctx* ctx, void* rho, void* rhou, void* rhov, void* rho
 
 /* Copies out the current primitive state (rho, u, v, p) via eq. (1). */
 lf_status lf_get_primitive(lf_ctx* ctx, void* rho, void* u, void* v, void* p, int on_device);
+
+/* Whole-state transfers for any dim and species count (the only state calls
+ * of 3D contexts; lf_set_state / lf_set_primitive / lf_get_state /
+ * lf_get_primitive return LF_ERR_ARG there).  U / q hold all nfields planes
+ * (see the conventions above).  The set calls reset t and the step count
+ * and compute the wave-speed maximum for the first dt, like lf_set_state;
+ * the primitive conversions use eq. (1) and run on the device. */
+lf_status lf_set_conservative(lf_ctx* ctx, const void* U, int on_device);
+lf_status lf_get_conservative(lf_ctx* ctx, void* U, int on_device);
+lf_status lf_set_primitives(lf_ctx* ctx, const void* q, int on_device);
+lf_status lf_get_primitives(lf_ctx* ctx, void* q, int on_device);
 
 /* Species (Sec. 5), for contexts with nspecies > 0 (LF_ERR_ARG otherwise).
  * Partial densities: rho_y holds nspecies planes of rho y_k, copied in or
@@ -163,9 +183,9 @@ lf_status lf_run(lf_ctx* ctx, double t_end, int32_t max_steps, int32_t* steps_do
 /* Current time and completed step count (synchronises). */
 lf_status lf_get_time(lf_ctx* ctx, double* t, int64_t* steps);
 
-/* Compensated (Neumaier) FP64 sums of the 4 + nspecies conservative fields
- * (rho, rho u, rho v, rho E, rho y_k) over all cells, in a fixed
- * (deterministic) reduction order.  out holds 4 + nspecies doubles;
+/* Compensated (Neumaier) FP64 sums of the nfields conservative fields
+ * (rho, rho u, rho v, [rho w,] rho E, rho y_k) over all cells, in a fixed
+ * (deterministic) reduction order.  out holds nfields doubles;
  * synchronises. */
 lf_status lf_conservation_sums(lf_ctx* ctx, double* out);
 

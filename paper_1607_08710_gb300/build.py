@@ -27,7 +27,8 @@ CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--exp
 # written out where wanted), so results do not depend on how an expression
 # was inlined.
 EXTRA = {"lf_kernels_f32.cu": ["-ftz=true", "-fmad=false"], "lf_kernels_f64.cu": ["-fmad=false"],
-         "lf_species_f32.cu": ["-ftz=true", "-fmad=false"], "lf_species_f64.cu": ["-fmad=false"]}
+         "lf_species_f32.cu": ["-ftz=true", "-fmad=false"], "lf_species_f64.cu": ["-fmad=false"],
+         "lf_kernels3d_f32.cu": ["-ftz=true", "-fmad=false"], "lf_kernels3d_f64.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:

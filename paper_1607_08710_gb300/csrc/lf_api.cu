@@ -38,17 +38,24 @@ namespace {
 
 const char* validate(const lf_config* c) {
   if (!c) return "config is NULL";
-  if (c->dim != 1 && c->dim != 2) return "dim must be 1 or 2";
+  if (c->dim < 1 || c->dim > 3) return "dim must be 1, 2 or 3";
   if (c->nx < 1 || c->ny < 1) return "nx and ny must be >= 1";
   if (c->dim == 1 && c->ny != 1) return "ny must be 1 when dim == 1";
-  if ((long long)c->nx * c->ny > (1LL << 31)) return "mesh larger than 2^31 cells";
+  if (c->dim < 3 && c->nz > 1) return "nz must be 0 or 1 below 3D";
+  if (c->dim == 3 && c->nz < 1) return "nz must be >= 1 in 3D";
+  if (c->nz < 0) return "nz must be >= 0";
+  const long long nz = c->dim == 3 ? c->nz : 1;
+  if ((long long)c->nx * c->ny * nz > (1LL << 31)) return "mesh larger than 2^31 cells";
+  if (c->dim == 3 && (!(c->zmax > c->zmin) || !std::isfinite(c->zmax - c->zmin))) return "need zmin < zmax";
+  if (c->dim == 3 && c->nspecies != 0) return "species are carried on 1D and 2D meshes";
+  if (c->reserved != 0) return "reserved must be 0";
   if (c->limiter < 0 || c->limiter > 2) return "unknown limiter";
   if (c->bc < 0 || c->bc > 1) return "unknown boundary condition";
   if (c->precision != LF_FP64 && c->precision != LF_FP32) return "unknown precision";
   if (c->riemann < 0 || c->riemann > 1) return "unknown interface solver";
   if (c->device < 0) return "device must be >= 0";
   if (!(c->xmax > c->xmin) || !std::isfinite(c->xmax - c->xmin)) return "need xmin < xmax";
-  if (c->dim == 2 && (!(c->ymax > c->ymin) || !std::isfinite(c->ymax - c->ymin))) return "need ymin < ymax";
+  if (c->dim >= 2 && (!(c->ymax > c->ymin) || !std::isfinite(c->ymax - c->ymin))) return "need ymin < ymax";
   if (!(c->gamma > 1.0 && c->gamma <= 3.0)) return "gamma must be in (1, 3]";
   if (!(c->cfl > 0.0 && c->cfl <= 1.0)) return "cfl must be in (0, 1]";
   if (c->limiter == LF_LIMITER_SWEBY && !(c->beta >= 1.0 && c->beta <= 2.0)) return "beta must be in [1, 2]";
@@ -88,13 +95,11 @@ lf_status dispatch_stage(lf_ctx* c, int stage) {
   cudaEvent_t stop = nullptr;
   if (c->profiling)
     if (lf_status st = trace_begin(c, stage == 0 ? 0 : 1, &stop)) return st;
-  cudaError_t e;
-  switch (stage) {
-    case 0: e = lf::launch_stage<T>(0, c->mesh, U, U, Us, c->sc, c->stream); break;
-    case 1: e = lf::launch_stage<T>(1, c->mesh, Us, U, U, c->sc, c->stream); break;
-    case 2: e = lf::launch_stage<T>(2, c->mesh, Us, U, U2, c->sc, c->stream); break;
-    default: e = lf::launch_stage<T>(3, c->mesh, U2, U, U, c->sc, c->stream);
-  }
+  const T* in[4] = {U, Us, Us, U2};
+  T* out[4] = {Us, U, U2, U};
+  const cudaError_t e = c->cfg.dim == 3
+                            ? lf::launch_stage3d(stage, c->mesh3, in[stage], U, out[stage], c->sc, c->stream)
+                            : lf::launch_stage<T>(stage, c->mesh, in[stage], U, out[stage], c->sc, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "stage launch");
   if (stop) LF_CUDA(c, cudaEventRecord(stop, c->stream));
   return LF_OK;
@@ -143,8 +148,13 @@ namespace {
 // Fresh time loop on the state just written into c->U.
 lf_status restart_clock(lf_ctx* c) {
   LF_CUDA(c, lf::launch_reset_scalars(c->sc, c->cfg.cfl, c->stream));
-  cudaError_t e = c->elem == 8 ? lf::launch_wave_speed<double>(c->mesh, static_cast<double*>(c->U), c->sc, c->stream)
-                               : lf::launch_wave_speed<float>(c->mesh, static_cast<float*>(c->U), c->sc, c->stream);
+  cudaError_t e;
+  if (c->cfg.dim == 3)
+    e = c->elem == 8 ? lf::launch_wave_speed3d(c->mesh3, static_cast<double*>(c->U), c->sc, c->stream)
+                     : lf::launch_wave_speed3d(c->mesh3, static_cast<float*>(c->U), c->sc, c->stream);
+  else
+    e = c->elem == 8 ? lf::launch_wave_speed<double>(c->mesh, static_cast<double*>(c->U), c->sc, c->stream)
+                     : lf::launch_wave_speed<float>(c->mesh, static_cast<float*>(c->U), c->sc, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "wave speed launch");
   c->has_state = true;
   return LF_OK;
@@ -175,8 +185,16 @@ lf_status copy_plane_out(lf_ctx* c, int l, void* dst, cudaMemcpyKind kind) {
 
 lf_status ensure_staging(lf_ctx* c) {
   if (c->staging) return LF_OK;
-  LF_CUDA(c, cudaMalloc(&c->staging, 4 * (size_t)c->mesh.nx * c->mesh.ny * c->elem));
+  const int planes = c->nf > 4 ? c->nf : 4;
+  LF_CUDA(c, cudaMalloc(&c->staging, planes * (size_t)c->mesh.nx * c->mesh.ny * c->elem));
   return LF_OK;
+}
+
+// The four-plane calls describe 1D/2D states only.
+lf_status reject_3d(lf_ctx* c, const char* who) {
+  if (c->cfg.dim != 3) return LF_OK;
+  set_err(c, "%s: 3D contexts transfer the whole state (lf_set_conservative / lf_set_primitives)", who);
+  return LF_ERR_ARG;
 }
 
 }  // namespace
@@ -263,7 +281,27 @@ lf_status lf_init(const lf_config* cfg, void* stream, lf_ctx** out) {
   m.vec = 1;  // pitch is a multiple of 128 bytes and the planes come from cudaMalloc
   m.nspecies = cfg->nspecies;
   static_assert(LF_MAX_SPECIES == lf::MAX_SPECIES, "public and kernel species limits agree");
-  const int nf = 4 + cfg->nspecies;
+  c->nf = 4 + cfg->nspecies;
+  if (cfg->dim == 3) {
+    lf::Mesh3Desc& m3 = c->mesh3;
+    m3.nx = cfg->nx;
+    m3.ny = cfg->ny;
+    m3.nz = cfg->nz;
+    m3.pitch = m.pitch;
+    m3.plane = (long long)m.pitch * cfg->ny * cfg->nz;
+    m3.bc = cfg->bc;
+    m3.limiter = cfg->limiter;
+    m3.riemann = cfg->riemann;
+    m3.nspecies = 0;
+    m3.gamma = m.gamma;
+    m3.beta = m.beta;
+    m3.rdx = m.rdx;
+    m3.rdy = cfg->ny / (cfg->ymax - cfg->ymin);
+    m3.rdz = cfg->nz / (cfg->zmax - cfg->zmin);
+    m = lf::mesh_view(m3, 0);  // the row view: copies and sums walk ny*nz rows
+    c->nf = 5;
+  }
+  const int nf = c->nf;
 
   DeviceGuard g(cfg->device);
   if (!g.ok) {
@@ -296,6 +334,7 @@ lf_status lf_init(const lf_config* cfg, void* stream, lf_ctx** out) {
 lf_status lf_set_state(lf_ctx* c, const void* rho, const void* rhou, const void* rhov, const void* rhoE,
                        int on_device) {
   if (!c) return LF_ERR_ARG;
+  if (lf_status st = reject_3d(c, "lf_set_state")) return st;
   if (!rho || !rhou || !rhoE || (c->cfg.dim == 2 && !rhov)) {
     set_err(c, "lf_set_state: NULL plane");
     return LF_ERR_ARG;
@@ -313,6 +352,7 @@ lf_status lf_set_state(lf_ctx* c, const void* rho, const void* rhou, const void*
 lf_status lf_set_primitive(lf_ctx* c, const void* rho, const void* u, const void* v, const void* p,
                            int on_device) {
   if (!c) return LF_ERR_ARG;
+  if (lf_status st = reject_3d(c, "lf_set_primitive")) return st;
   if (!rho || !u || !p || (c->cfg.dim == 2 && !v)) {
     set_err(c, "lf_set_primitive: NULL plane");
     return LF_ERR_ARG;
@@ -345,6 +385,7 @@ lf_status lf_set_primitive(lf_ctx* c, const void* rho, const void* u, const void
 
 lf_status lf_get_state(lf_ctx* c, void* rho, void* rhou, void* rhov, void* rhoE, int on_device) {
   if (!c) return LF_ERR_ARG;
+  if (lf_status st = reject_3d(c, "lf_get_state")) return st;
   if (!rho || !rhou || !rhoE || (c->cfg.dim == 2 && !rhov)) {
     set_err(c, "lf_get_state: NULL plane");
     return LF_ERR_ARG;
@@ -360,6 +401,7 @@ lf_status lf_get_state(lf_ctx* c, void* rho, void* rhou, void* rhov, void* rhoE,
 
 lf_status lf_get_primitive(lf_ctx* c, void* rho, void* u, void* v, void* p, int on_device) {
   if (!c) return LF_ERR_ARG;
+  if (lf_status st = reject_3d(c, "lf_get_primitive")) return st;
   if (!rho || !u || !p || (c->cfg.dim == 2 && !v)) {
     set_err(c, "lf_get_primitive: NULL plane");
     return LF_ERR_ARG;
@@ -471,6 +513,116 @@ lf_status lf_get_mass_fractions(lf_ctx* c, void* y, int on_device) {
   if (e != cudaSuccess) return cuda_fail(c, e, "cons_to_species launch");
   if (!on_device) {
     LF_CUDA(c, cudaMemcpyAsync(y, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
+    LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return LF_OK;
+}
+
+lf_status lf_set_conservative(lf_ctx* c, const void* U, int on_device) {
+  if (!c) return LF_ERR_ARG;
+  if (!U) {
+    set_err(c, "lf_set_conservative: NULL buffer");
+    return LF_ERR_ARG;
+  }
+  DeviceGuard g(c->cfg.device);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const size_t n = (size_t)c->mesh.nx * c->mesh.ny;
+  for (int l = 0; l < c->nf; ++l)
+    if (lf_status st = copy_plane_in(c, l, static_cast<const char*>(U) + l * n * c->elem, kind)) return st;
+  if (lf_status st = restart_clock(c)) return st;
+  if (!on_device) LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LF_OK;
+}
+
+lf_status lf_get_conservative(lf_ctx* c, void* U, int on_device) {
+  if (!c) return LF_ERR_ARG;
+  if (!U) {
+    set_err(c, "lf_get_conservative: NULL buffer");
+    return LF_ERR_ARG;
+  }
+  DeviceGuard g(c->cfg.device);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t n = (size_t)c->mesh.nx * c->mesh.ny;
+  for (int l = 0; l < c->nf; ++l)
+    if (lf_status st = copy_plane_out(c, l, static_cast<char*>(U) + l * n * c->elem, kind)) return st;
+  if (!on_device) LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LF_OK;
+}
+
+lf_status lf_set_primitives(lf_ctx* c, const void* q, int on_device) {
+  if (!c) return LF_ERR_ARG;
+  if (!q) {
+    set_err(c, "lf_set_primitives: NULL buffer");
+    return LF_ERR_ARG;
+  }
+  DeviceGuard g(c->cfg.device);
+  const size_t n = (size_t)c->mesh.nx * c->mesh.ny;
+  const char* src = static_cast<const char*>(q);
+  if (!on_device) {
+    if (lf_status st = ensure_staging(c)) return st;
+    LF_CUDA(c, cudaMemcpyAsync(c->staging, q, c->nf * n * c->elem, cudaMemcpyHostToDevice, c->stream));
+    src = static_cast<const char*>(c->staging);
+  }
+  cudaError_t e;
+  if (c->cfg.dim == 3) {
+    e = c->elem == 8 ? lf::launch_prim_to_cons3d(c->mesh3, (const double*)src, static_cast<double*>(c->U), c->stream)
+                     : lf::launch_prim_to_cons3d(c->mesh3, (const float*)src, static_cast<float*>(c->U), c->stream);
+  } else {
+    const size_t pb = n * c->elem;
+    if (c->elem == 8)
+      e = lf::launch_prim_to_cons<double>(c->mesh, (const double*)src, (const double*)(src + pb),
+                                          (const double*)(src + 2 * pb), (const double*)(src + 3 * pb), (long long)n,
+                                          static_cast<double*>(c->U), c->stream);
+    else
+      e = lf::launch_prim_to_cons<float>(c->mesh, (const float*)src, (const float*)(src + pb),
+                                         (const float*)(src + 2 * pb), (const float*)(src + 3 * pb), (long long)n,
+                                         static_cast<float*>(c->U), c->stream);
+    if (e == cudaSuccess && c->mesh.nspecies > 0)
+      e = c->elem == 8 ? lf::launch_species_to_cons<double>(c->mesh, (const double*)(src + 4 * pb),
+                                                           static_cast<double*>(c->U), c->stream)
+                       : lf::launch_species_to_cons<float>(c->mesh, (const float*)(src + 4 * pb),
+                                                          static_cast<float*>(c->U), c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "primitive conversion launch");
+  if (lf_status st = restart_clock(c)) return st;
+  if (!on_device) LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LF_OK;
+}
+
+lf_status lf_get_primitives(lf_ctx* c, void* q, int on_device) {
+  if (!c) return LF_ERR_ARG;
+  if (!q) {
+    set_err(c, "lf_get_primitives: NULL buffer");
+    return LF_ERR_ARG;
+  }
+  DeviceGuard g(c->cfg.device);
+  const size_t n = (size_t)c->mesh.nx * c->mesh.ny;
+  char* dst = static_cast<char*>(q);
+  if (!on_device) {
+    if (lf_status st = ensure_staging(c)) return st;
+    dst = static_cast<char*>(c->staging);
+  }
+  cudaError_t e;
+  if (c->cfg.dim == 3) {
+    e = c->elem == 8 ? lf::launch_cons_to_prim3d(c->mesh3, static_cast<const double*>(c->U), (double*)dst, c->stream)
+                     : lf::launch_cons_to_prim3d(c->mesh3, static_cast<const float*>(c->U), (float*)dst, c->stream);
+  } else {
+    const size_t pb = n * c->elem;
+    if (c->elem == 8)
+      e = lf::launch_cons_to_prim<double>(c->mesh, static_cast<double*>(c->U), (double*)dst, (double*)(dst + pb),
+                                          (double*)(dst + 2 * pb), (double*)(dst + 3 * pb), c->stream);
+    else
+      e = lf::launch_cons_to_prim<float>(c->mesh, static_cast<float*>(c->U), (float*)dst, (float*)(dst + pb),
+                                         (float*)(dst + 2 * pb), (float*)(dst + 3 * pb), c->stream);
+    if (e == cudaSuccess && c->mesh.nspecies > 0)
+      e = c->elem == 8 ? lf::launch_cons_to_species<double>(c->mesh, static_cast<const double*>(c->U),
+                                                           (double*)(dst + 4 * pb), c->stream)
+                       : lf::launch_cons_to_species<float>(c->mesh, static_cast<const float*>(c->U),
+                                                          (float*)(dst + 4 * pb), c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "primitive conversion launch");
+  if (!on_device) {
+    LF_CUDA(c, cudaMemcpyAsync(q, dst, c->nf * n * c->elem, cudaMemcpyDeviceToHost, c->stream));
     LF_CUDA(c, cudaStreamSynchronize(c->stream));
   }
   return LF_OK;
@@ -594,13 +746,15 @@ lf_status lf_get_time(lf_ctx* c, double* t, int64_t* steps) {
 lf_status lf_conservation_sums(lf_ctx* c, double* out) {
   if (!c || !out) return LF_ERR_ARG;
   DeviceGuard g(c->cfg.device);
-  cudaError_t e = c->elem == 8 ? lf::launch_sums<double>(c->mesh, static_cast<double*>(c->U), c->partials,
+  // planes past the first four are summed as the view's extra planes
+  lf::MeshDesc view = c->mesh;
+  view.nspecies = c->nf - 4;
+  cudaError_t e = c->elem == 8 ? lf::launch_sums<double>(view, static_cast<double*>(c->U), c->partials,
                                                          lf::sums_blocks(), c->dsums, c->stream)
-                               : lf::launch_sums<float>(c->mesh, static_cast<float*>(c->U), c->partials,
+                               : lf::launch_sums<float>(view, static_cast<float*>(c->U), c->partials,
                                                         lf::sums_blocks(), c->dsums, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "sums launch");
-  LF_CUDA(c, cudaMemcpyAsync(out, c->dsums, (4 + c->mesh.nspecies) * sizeof(double), cudaMemcpyDeviceToHost,
-                             c->stream));
+  LF_CUDA(c, cudaMemcpyAsync(out, c->dsums, c->nf * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   LF_CUDA(c, cudaStreamSynchronize(c->stream));
   return LF_OK;
 }

@@ -8,20 +8,23 @@
 
 #include "../../include/lagflux.h"
 #include "lf_internal.h"
+#include "lf_internal3d.h"
 
 struct lf_ctx {
   lf_config cfg;
-  lf::MeshDesc mesh;
+  lf::MeshDesc mesh;          // 1D/2D mesh; for 3D the row view (ny*nz rows of nx cells)
+  lf::Mesh3Desc mesh3{};      // 3D meshes only
+  int nf = 4;                 // state planes: 4 (+1 in 3D) + nspecies
   cudaStream_t stream = nullptr;
   size_t elem = 8;            // bytes per element
-  void* U = nullptr;          // current state, 4 pitched planes
-  void* Ustar = nullptr;      // Heun predictor / first RK3 stage, 4 pitched planes
+  void* U = nullptr;          // current state, nf pitched planes
+  void* Ustar = nullptr;      // Heun predictor / first RK3 stage, nf pitched planes
   void* U2 = nullptr;         // second SSP-RK3 stage (time_order 3 only)
-  void* staging = nullptr;    // dense 4 planes for host primitive transfers (lazy)
+  void* staging = nullptr;    // dense max(4, nf) planes for host transfers (lazy)
   lf::Scalars* sc = nullptr;  // device scalars
   lf::Scalars* hsc = nullptr; // pinned host mirror for read-back
   double* partials = nullptr; // conservation-sum partials
-  double* dsums = nullptr;    // 4 device doubles
+  double* dsums = nullptr;    // nf device doubles
   bool has_state = false;
   // lf_run replays a CUDA graph of kRunBatch steps (recorded once, on a
   // private stream; replayed on `stream`)

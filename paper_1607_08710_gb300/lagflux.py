@@ -44,6 +44,10 @@ class lf_config(ctypes.Structure):
         ("gamma", ctypes.c_double),
         ("cfl", ctypes.c_double),
         ("beta", ctypes.c_double),
+        ("nz", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("zmin", ctypes.c_double),
+        ("zmax", ctypes.c_double),
     ]
 
 
@@ -58,6 +62,10 @@ SIGNATURES = {
     "lf_set_primitive": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
     "lf_get_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
     "lf_get_primitive": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
+    "lf_set_conservative": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "lf_get_conservative": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "lf_set_primitives": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "lf_get_primitives": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "lf_set_partial_densities": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "lf_get_partial_densities": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "lf_set_mass_fractions": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
@@ -127,11 +135,26 @@ class Config:
     device: int = 0
     time_order: int = 2  # 2: Heun (Sec. 4), 3: SSP-RK3
     nspecies: int = 0  # transported mass fractions (Sec. 5), 0 .. MAX_SPECIES
+    nz: int = 1
+    zmin: float = 0.0
+    zmax: float = 1.0
 
     def to_c(self) -> lf_config:
-        return lf_config(self.dim, self.nx, self.ny if self.dim == 2 else 1, LIMITERS[self.limiter], BCS[self.bc],
+        return lf_config(self.dim, self.nx, self.ny if self.dim >= 2 else 1, LIMITERS[self.limiter], BCS[self.bc],
                          PRECISIONS[self.precision], RIEMANN[self.riemann], self.device, self.time_order,
-                         self.nspecies, self.xmin, self.xmax, self.ymin, self.ymax, self.gamma, self.cfl, self.beta)
+                         self.nspecies, self.xmin, self.xmax, self.ymin, self.ymax, self.gamma, self.cfl, self.beta,
+                         self.nz if self.dim == 3 else 1, 0, self.zmin, self.zmax)
+
+    @property
+    def nfields(self) -> int:
+        """Planes of a whole state: 4 (5 in 3D) + nspecies."""
+        return (5 if self.dim == 3 else 4) + self.nspecies
+
+    @property
+    def shape(self) -> tuple:
+        """Shape of one plane: (ny, nx), or (nz, ny, nx) in 3D."""
+        ny = self.ny if self.dim >= 2 else 1
+        return (self.nz, ny, self.nx) if self.dim == 3 else (ny, self.nx)
 
     @property
     def np_dtype(self):
@@ -230,6 +253,40 @@ class LagrangeFlux:
         self._check(_lib.lf_get_primitive(self._h, *ptrs, k))
         return out
 
+    # -- whole-state transfers (any dim, species included) ---------------
+    def _state_buffer(self, a):
+        n = self.cfg.nfields * int(np.prod(self.cfg.shape))
+        p, k = _ptr_and_kind(a)
+        if int(np.prod(a.shape)) != n:
+            raise ValueError(f"state buffer has {int(np.prod(a.shape))} elements, expected {n}")
+        self._check_dtype(a)
+        return p, k
+
+    def _state_out(self, out):
+        return np.empty((self.cfg.nfields,) + self.cfg.shape, dtype=self.cfg.np_dtype) if out is None else out
+
+    def set_conservative(self, U):
+        """U: (nfields,) + shape conservative planes (rho, rho u, rho v, [rho w,] rho E, rho y_k)."""
+        p, k = self._state_buffer(U)
+        self._check(_lib.lf_set_conservative(self._h, p, k))
+
+    def get_conservative(self, out=None):
+        out = self._state_out(out)
+        p, k = self._state_buffer(out)
+        self._check(_lib.lf_get_conservative(self._h, p, k))
+        return out
+
+    def set_primitives(self, q):
+        """q: (nfields,) + shape primitive planes (rho, u, v, [w,] p, y_k)."""
+        p, k = self._state_buffer(q)
+        self._check(_lib.lf_set_primitives(self._h, p, k))
+
+    def get_primitives(self, out=None):
+        out = self._state_out(out)
+        p, k = self._state_buffer(out)
+        self._check(_lib.lf_get_primitives(self._h, p, k))
+        return out
+
     # -- species (Sec. 5) -------------------------------------------------
     def _species_buffer(self, a):
         ny = self.cfg.ny if self.cfg.dim == 2 else 1
@@ -291,8 +348,8 @@ class LagrangeFlux:
         return t.value, s.value
 
     def conservation_sums(self) -> np.ndarray:
-        """FP64 sums of the 4 + nspecies conservative fields."""
-        out = (ctypes.c_double * (4 + self.cfg.nspecies))()
+        """FP64 sums of the nfields conservative fields."""
+        out = (ctypes.c_double * self.cfg.nfields)()
         self._check(_lib.lf_conservation_sums(self._h, out))
         return np.array(out[:])
 

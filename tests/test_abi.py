@@ -63,7 +63,7 @@ def test_status_strings(lib):
 
 @pytest.mark.parametrize(
     "field,value",
-    [("dim", 3), ("nx", 0), ("ny", 0), ("limiter", 7), ("bc", 2), ("precision", 5), ("riemann", 2), ("gamma", 1.0),
+    [("dim", 4), ("dim", 0), ("nz", 2), ("reserved", 1), ("nx", 0), ("ny", 0), ("limiter", 7), ("bc", 2), ("precision", 5), ("riemann", 2), ("gamma", 1.0),
      ("gamma", 3.5), ("cfl", 0.0), ("cfl", 1.5), ("beta", 2.5), ("xmax", 0.0), ("device", -1), ("nspecies", 3),
      ("nspecies", -1), ("time_order", 4)],
 )
@@ -74,6 +74,15 @@ def test_init_rejects_bad_config_without_gpu(lib, field, value):
     st = lib.lf_init(ctypes.byref(cfg), None, ctypes.byref(h))
     assert st == lib.LF_ERR_ARG
     assert h.value is None
+    assert b"invalid configuration" in lib.lf_last_error(None)
+
+
+@pytest.mark.parametrize("field,value", [("zmax", 0.0), ("nz", 0), ("nspecies", 1)])
+def test_init_rejects_bad_3d_config_without_gpu(lib, field, value):
+    cfg = lib.Config(nx=8, ny=8, nz=8, dim=3).to_c()
+    setattr(cfg, field, value)
+    h = ctypes.c_void_p()
+    assert lib.lf_init(ctypes.byref(cfg), None, ctypes.byref(h)) == lib.LF_ERR_ARG
     assert b"invalid configuration" in lib.lf_last_error(None)
 
 
