@@ -17,8 +17,9 @@
 // two copies are bitwise equal and the update stays conservative.
 //
 // Memory.  The input planes (the CTA's rows plus halo rows, all fields) are
-// staged into a shared ring four planes deep by cp.async, every thread
-// copying a share; the U^n rows of the later stages into a two-plane ring.
+// staged into a shared ring four planes deep by cp.async, each warp copying
+// its own row and warps 0-3 one halo row each; the U^n rows of the later
+// stages into a two-plane ring.
 // One commit group per plane: at the top of a step the group issued one step
 // earlier is complete and a barrier makes it visible to the whole CTA.
 // Every global index is mapped into the mesh by the boundary condition, and
@@ -32,13 +33,13 @@
 namespace lf {
 
 #ifndef LF_3D_ROWS
-#define LF_3D_ROWS 6
+#define LF_3D_ROWS 4
 #endif
 #ifndef LF_3D_TZ
-#define LF_3D_TZ 32
+#define LF_3D_TZ 64
 #endif
 #ifndef LF_3D_MIN_BLOCKS
-#define LF_3D_MIN_BLOCKS 2
+#define LF_3D_MIN_BLOCKS 3
 #endif
 constexpr int ROWS3 = LF_3D_ROWS;  // output rows (warps) per CTA
 constexpr int TZ3 = LF_3D_TZ;      // planes per z-tile
@@ -111,22 +112,28 @@ struct Args3 {
   T* P;     // primitives of the current plane, all CTA rows
   T* unr;   // RUN3 U^n planes
   int j0, k0, kend;
+  long long own_off;   // element offset of this warp's (mapped) row in a plane of rows
+  long long halo_off;  // the same for the halo row this warp copies (warps 0-3)
+  int halo_rr;         // that halo row's index in the CTA's rows (-1: none)
 };
 
-// This thread's share of the copies of input plane `k` (all CTA rows, all
-// fields) into its ring slot: (row, field) segments are dealt to the warps in
-// turn, each lane copying its own CPL cells.
+// This warp's copies of input plane `k` into its ring slot: its own row and,
+// for warps 0-3, one halo row, all fields, each lane copying its own CPL cells.
 template <typename T, int STAGE, int CPL, int NF>
 __device__ __forceinline__ void issue_plane3(const Mesh3Desc& m, const Args3<T, STAGE, NF>& A, const LaneCols<CPL>& L,
                                              int k, int warp, int lane) {
   using SM = Smem3<T, CPL, NF>;
-  const int zm = map_row(k, m.nz, m.bc);
-  T* slot = A.ring + ((k - A.k0 + 4) & 3) * SM::PLANE_IN;
-  for (int p = warp; p < (ROWS3 + HALO3) * NF; p += ROWS3) {
-    const int rr = p / NF, f = p - rr * NF;
-    const int y = map_row(A.j0 - 2 + rr, m.ny, m.bc);
-    const T* src = A.Uin + f * m.plane + ((long long)zm * m.ny + y) * m.pitch;
-    copy_cells<T, CPL>(slot + rr * SM::ROWSEG + f * 32 * CPL + CPL * lane, src, L);
+  const long long zoff = (long long)map_row(k, m.nz, m.bc) * m.ny * m.pitch;
+  T* slot = A.ring + ((k - A.k0 + 4) & 3) * SM::PLANE_IN + CPL * lane;
+  const T* src = A.Uin + zoff + A.own_off;
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+    copy_cells<T, CPL>(slot + (warp + 2) * SM::ROWSEG + f * 32 * CPL, src + f * m.plane, L);
+  if (A.halo_rr >= 0) {
+    const T* hsrc = A.Uin + zoff + A.halo_off;
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+      copy_cells<T, CPL>(slot + A.halo_rr * SM::ROWSEG + f * 32 * CPL, hsrc + f * m.plane, L);
   }
 }
 
@@ -176,8 +183,8 @@ __device__ __forceinline__ void march_plane3(const Phys<V>& P, const Mesh3Desc& 
   }
   // publish this row's primitives of plane k; warps 0-3 convert the halo rows
   write_seg<T, CPL, NF>(A.P + (warp + 2) * SM::ROWSEG, lane, M.q[S]);
-  if (warp < HALO3) {
-    const int rr = warp < 2 ? warp : ROWS3 + warp;
+  if (A.halo_rr >= 0) {
+    const int rr = A.halo_rr;
     V Uh[NF], qh[NF];
     read_seg<T, CPL, NF>(slot_k + rr * SM::ROWSEG, lane, Uh);
     to_prim3<V, NF>(P, Uh, qh);
@@ -322,6 +329,9 @@ stage3d_kernel(const Mesh3Desc m, const T* __restrict__ Uin, const T* Un, T* out
   A.j0 = j0;
   A.k0 = blockIdx.z * TZ3;
   A.kend = min(A.k0 + TZ3, m.nz);
+  A.own_off = (long long)map_row(jrow, m.ny, m.bc) * m.pitch;
+  A.halo_rr = warp < HALO3 ? (warp < 2 ? warp : ROWS3 + warp) : -1;
+  A.halo_off = A.halo_rr >= 0 ? (long long)map_row(j0 - 2 + A.halo_rr, m.ny, m.bc) * m.pitch : 0;
   const LaneCols<CPL> L = lane_cols<CPL>(i0, lane, m.nx, m.bc, 1);
   const double hs = StageCoef<STAGE>::beta;
   const V ncx = V(-T(hs * dtd * m.rdx)), ncy = V(-T(hs * dtd * m.rdy)), ncz = V(-T(hs * dtd * m.rdz));
