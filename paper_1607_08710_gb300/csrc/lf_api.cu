@@ -164,6 +164,9 @@ char* plane_ptr(lf_ctx* c, void* base, int l) {
   return static_cast<char*>(base) + (size_t)l * c->mesh.plane * c->elem;
 }
 
+// Dense caller planes <-> pitched state planes.  When the rows carry no
+// padding (nx a multiple of the row alignment) a plane is one contiguous
+// block and moves as a single copy.
 lf_status copy_plane_in(lf_ctx* c, int l, const void* src, cudaMemcpyKind kind) {
   const size_t w = (size_t)c->mesh.nx * c->elem;
   char* dst = plane_ptr(c, c->U, l);
@@ -171,15 +174,21 @@ lf_status copy_plane_in(lf_ctx* c, int l, const void* src, cudaMemcpyKind kind) 
     LF_CUDA(c, cudaMemset2DAsync(dst, (size_t)c->mesh.pitch * c->elem, 0, w, c->mesh.ny, c->stream));
     return LF_OK;
   }
-  LF_CUDA(c, cudaMemcpy2DAsync(dst, (size_t)c->mesh.pitch * c->elem, src, w, w, c->mesh.ny, kind, c->stream));
+  if (c->mesh.pitch == c->mesh.nx)
+    LF_CUDA(c, cudaMemcpyAsync(dst, src, w * c->mesh.ny, kind, c->stream));
+  else
+    LF_CUDA(c, cudaMemcpy2DAsync(dst, (size_t)c->mesh.pitch * c->elem, src, w, w, c->mesh.ny, kind, c->stream));
   return LF_OK;
 }
 
 lf_status copy_plane_out(lf_ctx* c, int l, void* dst, cudaMemcpyKind kind) {
   if (!dst) return LF_OK;
   const size_t w = (size_t)c->mesh.nx * c->elem;
-  LF_CUDA(c, cudaMemcpy2DAsync(dst, w, plane_ptr(c, c->U, l), (size_t)c->mesh.pitch * c->elem, w, c->mesh.ny,
-                               kind, c->stream));
+  if (c->mesh.pitch == c->mesh.nx)
+    LF_CUDA(c, cudaMemcpyAsync(dst, plane_ptr(c, c->U, l), w * c->mesh.ny, kind, c->stream));
+  else
+    LF_CUDA(c, cudaMemcpy2DAsync(dst, w, plane_ptr(c, c->U, l), (size_t)c->mesh.pitch * c->elem, w, c->mesh.ny,
+                                 kind, c->stream));
   return LF_OK;
 }
 

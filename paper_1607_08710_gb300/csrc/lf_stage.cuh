@@ -46,7 +46,7 @@ namespace lf {
 #define LF_MIN_BLOCKS0 18
 #endif
 #ifndef LF_MIN_BLOCKS1
-#define LF_MIN_BLOCKS1 16
+#define LF_MIN_BLOCKS1 17
 #endif
 constexpr int STAGE_WARPS = LF_STAGE_WARPS;  // warps per CTA, side by side in x
 

@@ -177,3 +177,28 @@ def test_3d_argument_errors():
         s.adjoint_forward(2)
     assert ei.value.status == 1
     s.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (40, 1, 1), (1, 1, 33), (1, 17, 1), (3, 2, 2), (65, 5, 3)])
+@pytest.mark.parametrize("bc", ["transmissive", "periodic"])
+def test_degenerate_and_thin_meshes_fp64(shape, bc):
+    """Meshes of one cell along some axes (the step must reduce to the lower-
+    dimensional scheme there) and tiny meshes smaller than one strip, one
+    row block or one z-tile."""
+    nz, ny, nx = shape
+    q = inputs.octant(nx, ny, nz, seed=7).stack()
+    kw = dict(bc=bc, limiter="vanleer", cfl=0.4)
+    ref = oracle3(q, 12, **kw)
+    U, _, _ = gpu3(q, "fp64", steps=12, **kw)
+    assert_close(U, ref.U, FP64_TOL)
+
+
+def test_nonphysical_state_is_flagged_3d():
+    q = inputs.octant(16, 12, 10, seed=1).stack()
+    q[4, 5, 6, 7] = -0.5  # negative pressure in one cell
+    s = LagrangeFlux(Config(nx=16, ny=12, nz=10, dim=3))
+    s.set_primitives(np.ascontiguousarray(q))
+    with pytest.raises(LagrangeFluxError) as ei:
+        s.run(max_steps=3)
+    assert ei.value.status == 4  # LF_ERR_NONPHYSICAL
+    s.close()
