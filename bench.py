@@ -34,6 +34,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "cell-updates/s"
+# The paper's own multicore-CPU throughput for the Lagrange-flux scheme (Sec. 5, performance
+# table): context only, another machine; it states neither precision nor mesh size.
+PAPER_CPU_CONTEXT = {
+    "value": 81.0e6, "unit": METRIC, "note": "context only (other hardware, precision and mesh not stated)",
+    "hardware": "2x Intel Xeon E5-2670 (Sandy Bridge, 16 cores, AVX, OpenMP)",
+    "single_core": {"scalar": 2.6e6, "avx": 5.8e6}, "source": "arXiv:1607.08710, Sec. 5, performance table",
+}
 BYTES_PER_CELL = {  # algorithmic bytes per cell per launch: words read + written x word size
     ("stage0", "fp32"): 8 * 4, ("stage1", "fp32"): 12 * 4,
     ("stage0", "fp64"): 8 * 8, ("stage1", "fp64"): 12 * 8,
@@ -570,6 +577,7 @@ def run_ours(args, dist):
         "roofline": roofline, "kernels": kernels, "gpu_launches": 4 * args.steps, "clocks": clk,
     }
     line.update(out)
+    line["paper_cpu_context"] = PAPER_CPU_CONTEXT
     if not args.no_cpu_baseline and dist.world == 1:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)
