@@ -34,7 +34,7 @@ __device__ __forceinline__ void lagrange_flux3(const Phys<V>& P, const V qL[NF],
   const V ndu = unL - unR, ndp = pL - pR;
   V pstar, ustar;
   if (P.riemann == RIEMANN_MAXC) {
-    const V a2 = P.gamma * vmax(Ar<V>::div(pL, rL), Ar<V>::div(pR, rR));
+    const V a2 = P.gamma * max_quotient(pL, rL, pR, rR);
     V a, ia;
     Ar<V>::sqrt_and_rsqrt(a2, a, ia);
     const V irs = Ar<V>::rcp(rL + rR);

@@ -26,6 +26,8 @@
 // only output cells (column < nx, row < ny, plane < nz) are stored.
 #pragma once
 
+#include <atomic>
+
 #include "lf_device3d.cuh"
 #include "lf_internal3d.h"
 #include "lf_stage.cuh"
@@ -349,7 +351,7 @@ stage3d_kernel(const Mesh3Desc m, const T* __restrict__ Uin, const T* Un, T* out
   March3<V, NF> M;
   {
     V Ut[NF], qm2[NF];
-    const int slot_of[4] = {-1, 2, 0, 1};
+    const int slot_of[4] = {-1, 2, 0, 1};  // register slots of planes k0-1 .. k0+1 (k0-2 goes to qm2)
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       read_seg<T, CPL, NF>(A.ring + ((k0 - 2 + t - k0 + 4) & 3) * SM::PLANE_IN + (warp + 2) * SM::ROWSEG, lane, Ut);
@@ -395,16 +397,17 @@ cudaError_t launch_stage3d_lim(int stage, const Mesh3Desc& m, const T* Uin, cons
   cudaError_t e = cudaSuccess;
   switch (stage) {
 // The shared-memory opt-in is a per-device function attribute, set before the
-// first launch on each device.
+// first launch on each device (setting it twice is harmless, so the flags
+// only need to be atomic, not ordered).
 #define LF_STAGE3_CASE(ST)                                                                                    \
   case ST: {                                                                                                  \
-    static bool opted[64] = {};                                                                               \
+    static std::atomic<bool> opted[64];                                                                       \
     int dev = 0;                                                                                              \
     e = cudaGetDevice(&dev);                                                                                  \
-    if (e == cudaSuccess && (dev >= 64 || !opted[dev])) {                                                     \
+    if (e == cudaSuccess && (dev >= 64 || !opted[dev].load(std::memory_order_relaxed))) {                     \
       e = cudaFuncSetAttribute(stage3d_kernel<T, LIM, ST, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                                (int)SM::bytes(ST));                                                           \
-      if (e == cudaSuccess && dev < 64) opted[dev] = true;                                                    \
+      if (e == cudaSuccess && dev < 64) opted[dev].store(true, std::memory_order_relaxed);                    \
     }                                                                                                         \
     if (e == cudaSuccess) stage3d_kernel<T, LIM, ST, NF><<<grid, block, smem, s>>>(m, Uin, Un, out, sc);      \
     break;                                                                                                    \
