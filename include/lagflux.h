@@ -79,7 +79,7 @@ enum { LF_FP64 = 0, LF_FP32 = 1 };
 /* Interface solver: eqs. (13)-(14) with a = max(c_L, c_R) (default), or the
  * acoustic solver with per-side impedances Z_k = rho_k c_k. */
 enum { LF_RIEMANN_MAXC = 0, LF_RIEMANN_PER_SIDE = 1 };
-/* Time integrator (Sec. 4: "RK2, etc."): the Heun scheme of Sec. 4 (0 or 2),
+/* Time integrator (Sec. 4 leaves the Runge-Kutta family open): the Heun scheme of Sec. 4 (0 or 2),
  * or the third-order strong-stability-preserving Runge-Kutta scheme of Shu
  * and Osher (3), U1 = U + dt L(U), U2 = 3/4 U + 1/4 (U1 + dt L(U1)),
  * U' = 1/3 U + 2/3 (U2 + dt L(U2)).  SSP-RK3 needs one more state buffer and

@@ -1,7 +1,7 @@
 """Exact solution of the 1D Riemann problem for the ideal-gas Euler equations.
 
-TEST INFRASTRUCTURE ONLY.  The paper compares its shock-tube results with "the
-analytic solution" (Sec. 4.2, all four tubes); this module supplies that
+TEST INFRASTRUCTURE ONLY.  The paper compares its shock-tube results with the
+exact solution (Sec. 4.2, all four tubes); this module supplies that
 solution so the oracle can be pinned against it.  It follows the classical
 construction in Toro's book (cited by the paper as [Toro], ch. 4):
 

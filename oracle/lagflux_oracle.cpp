@@ -16,8 +16,8 @@
 //
 // Readings of points where the paper is silent (each is repeated in the
 // design notes):
-//   * CFL condition (Sec. 4, Heun step 1 only says "subject to some CFL
-//     condition"): dt = CFL / max_K sum_d (|u_d,K| + c_K) / dx_d over the
+//   * CFL condition (Sec. 4, Heun step 1 requires a CFL condition without
+//     writing it out): dt = CFL / max_K sum_d (|u_d,K| + c_K) / dx_d over the
 //     mesh's axes (1D: x; 2D: x, y; 3D: x, y, z), from U^n, the same dt for
 //     all stages; clipped to t_end - t when a final time is given.
 //   * Three dimensions (the finite-volume form of Sec. 4 is written for any
@@ -422,7 +422,7 @@ bool heun_step(const OracleConfig& c, std::vector<S> U[], double dt) {
 
 // Third-order strong-stability-preserving Runge-Kutta step of Shu and Osher
 // (J. Comput. Phys. 77, 1988) for the semi-discrete scheme dU/dt = L(U),
-// L(U) = -(1/|K|) sum_A |A| Phi_A (Sec. 4 names "RK2, etc." as time advance
+// L(U) = -(1/|K|) sum_A |A| Phi_A (Sec. 4 leaves the Runge-Kutta family open as time advance
 // schemes):
 //   U1 = U^n + dt L(U^n)
 //   U2 = 3/4 U^n + 1/4 (U1 + dt L(U1))
