@@ -22,7 +22,8 @@
  *     double for LF_FP64, float for LF_FP32.  The conservative planes are
  *     (rho, rho u, rho v, rho E); the primitive planes (rho, u, v, p).
  *     Species planes (nspecies > 0) are passed as one buffer of nspecies
- *     consecutive planes: partial densities rho y_k or mass fractions y_k.
+ *     consecutive planes (nx*ny*nz values each in 3D): partial densities
+ *     rho y_k or mass fractions y_k.
  *     The whole-state calls (lf_set_conservative and friends) take one
  *     buffer of all nfields planes: (rho, rho u, rho v, [rho w,] rho E,
  *     rho y_k) or (rho, u, v, [w,] p, y_k), nfields = 4 (5 in 3D) + nspecies,
@@ -98,8 +99,8 @@ typedef struct lf_config {
   int32_t device;    /* CUDA device ordinal */
   int32_t time_order; /* LF_TIME_* (0 = LF_TIME_HEUN) */
   int32_t nspecies;  /* transported mass fractions, 0 .. LF_MAX_SPECIES (Sec. 5);
-                        lf_init contexts of dim 1 or 2 only (0 for 3D,
-                        batches, the adjoint and lf_step_noalloc) */
+                        lf_init contexts (0 for batches, the adjoint and
+                        lf_step_noalloc) */
   double xmin, xmax; /* domain in x */
   double ymin, ymax; /* domain in y (ignored in 1D) */
   double gamma;      /* ratio of specific heats, 1 < gamma <= 3 (Sec. 3) */
@@ -113,7 +114,7 @@ typedef struct lf_config {
 typedef struct lf_ctx lf_ctx;
 
 /* Creates a solver for one mesh.  `stream` is a cudaStream_t (NULL: default
- * stream).  Allocates the device state (4 + nspecies planes), one
+ * stream).  Allocates the device state (nfields planes), one
  * intermediate Heun state (as many planes; two for SSP-RK3) and a few
  * scalars.  The species planes start at 0.  *out is set only on LF_OK. */
 lf_status lf_init(const lf_config* cfg, void* stream, lf_ctx** out);

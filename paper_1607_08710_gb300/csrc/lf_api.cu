@@ -47,7 +47,6 @@ const char* validate(const lf_config* c) {
   const long long nz = c->dim == 3 ? c->nz : 1;
   if ((long long)c->nx * c->ny * nz > (1LL << 31)) return "mesh larger than 2^31 cells";
   if (c->dim == 3 && (!(c->zmax > c->zmin) || !std::isfinite(c->zmax - c->zmin))) return "need zmin < zmax";
-  if (c->dim == 3 && c->nspecies != 0) return "species are carried on 1D and 2D meshes";
   if (c->reserved != 0) return "reserved must be 0";
   if (c->limiter < 0 || c->limiter > 2) return "unknown limiter";
   if (c->bc < 0 || c->bc > 1) return "unknown boundary condition";
@@ -291,6 +290,8 @@ lf_status lf_init(const lf_config* cfg, void* stream, lf_ctx** out) {
   m.nspecies = cfg->nspecies;
   static_assert(LF_MAX_SPECIES == lf::MAX_SPECIES, "public and kernel species limits agree");
   c->nf = 4 + cfg->nspecies;
+  c->nspecies = cfg->nspecies;
+  c->sp0 = 4;
   if (cfg->dim == 3) {
     lf::Mesh3Desc& m3 = c->mesh3;
     m3.nx = cfg->nx;
@@ -301,14 +302,15 @@ lf_status lf_init(const lf_config* cfg, void* stream, lf_ctx** out) {
     m3.bc = cfg->bc;
     m3.limiter = cfg->limiter;
     m3.riemann = cfg->riemann;
-    m3.nspecies = 0;
+    m3.nspecies = cfg->nspecies;
     m3.gamma = m.gamma;
     m3.beta = m.beta;
     m3.rdx = m.rdx;
     m3.rdy = cfg->ny / (cfg->ymax - cfg->ymin);
     m3.rdz = cfg->nz / (cfg->zmax - cfg->zmin);
     m = lf::mesh_view(m3, 0);  // the row view: copies and sums walk ny*nz rows
-    c->nf = 5;
+    c->nf = 5 + cfg->nspecies;
+    c->sp0 = 5;
   }
   const int nf = c->nf;
 
@@ -446,7 +448,7 @@ lf_status lf_get_primitive(lf_ctx* c, void* rho, void* u, void* v, void* p, int 
 namespace {
 
 lf_status species_args(lf_ctx* c, const void* p, const char* who) {
-  if (c->mesh.nspecies == 0) {
+  if (c->nspecies == 0) {
     set_err(c, "%s: the context carries no species (nspecies == 0)", who);
     return LF_ERR_ARG;
   }
@@ -467,8 +469,9 @@ lf_status lf_set_partial_densities(lf_ctx* c, const void* rho_y, int on_device) 
   DeviceGuard g(c->cfg.device);
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const size_t n = (size_t)c->mesh.nx * c->mesh.ny;
-  for (int k = 0; k < c->mesh.nspecies; ++k)
-    if (lf_status st = copy_plane_in(c, 4 + k, static_cast<const char*>(rho_y) + k * n * c->elem, kind)) return st;
+  for (int k = 0; k < c->nspecies; ++k)
+    if (lf_status st = copy_plane_in(c, c->sp0 + k, static_cast<const char*>(rho_y) + k * n * c->elem, kind))
+      return st;
   if (!on_device) LF_CUDA(c, cudaStreamSynchronize(c->stream));
   return LF_OK;
 }
@@ -479,8 +482,8 @@ lf_status lf_get_partial_densities(lf_ctx* c, void* rho_y, int on_device) {
   DeviceGuard g(c->cfg.device);
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   const size_t n = (size_t)c->mesh.nx * c->mesh.ny;
-  for (int k = 0; k < c->mesh.nspecies; ++k)
-    if (lf_status st = copy_plane_out(c, 4 + k, static_cast<char*>(rho_y) + k * n * c->elem, kind)) return st;
+  for (int k = 0; k < c->nspecies; ++k)
+    if (lf_status st = copy_plane_out(c, c->sp0 + k, static_cast<char*>(rho_y) + k * n * c->elem, kind)) return st;
   if (!on_device) LF_CUDA(c, cudaStreamSynchronize(c->stream));
   return LF_OK;
 }
@@ -489,17 +492,24 @@ lf_status lf_set_mass_fractions(lf_ctx* c, const void* y, int on_device) {
   if (!c) return LF_ERR_ARG;
   if (lf_status st = species_args(c, y, "lf_set_mass_fractions")) return st;
   DeviceGuard g(c->cfg.device);
-  const size_t bytes = (size_t)c->mesh.nspecies * c->mesh.nx * c->mesh.ny * c->elem;
+  const size_t bytes = (size_t)c->nspecies * c->mesh.nx * c->mesh.ny * c->elem;
   const void* src = y;
   if (!on_device) {
     if (lf_status st = ensure_staging(c)) return st;  // 4 planes >= LF_MAX_SPECIES planes
     LF_CUDA(c, cudaMemcpyAsync(c->staging, y, bytes, cudaMemcpyHostToDevice, c->stream));
     src = c->staging;
   }
-  cudaError_t e = c->elem == 8 ? lf::launch_species_to_cons<double>(c->mesh, static_cast<const double*>(src),
-                                                                   static_cast<double*>(c->U), c->stream)
-                               : lf::launch_species_to_cons<float>(c->mesh, static_cast<const float*>(src),
-                                                                  static_cast<float*>(c->U), c->stream);
+  cudaError_t e;
+  if (c->cfg.dim == 3)
+    e = c->elem == 8 ? lf::launch_species_to_cons3d(c->mesh3, static_cast<const double*>(src),
+                                                    static_cast<double*>(c->U), c->stream)
+                     : lf::launch_species_to_cons3d(c->mesh3, static_cast<const float*>(src),
+                                                    static_cast<float*>(c->U), c->stream);
+  else
+    e = c->elem == 8 ? lf::launch_species_to_cons<double>(c->mesh, static_cast<const double*>(src),
+                                                         static_cast<double*>(c->U), c->stream)
+                     : lf::launch_species_to_cons<float>(c->mesh, static_cast<const float*>(src),
+                                                        static_cast<float*>(c->U), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "species_to_cons launch");
   if (!on_device) LF_CUDA(c, cudaStreamSynchronize(c->stream));
   return LF_OK;
@@ -509,16 +519,23 @@ lf_status lf_get_mass_fractions(lf_ctx* c, void* y, int on_device) {
   if (!c) return LF_ERR_ARG;
   if (lf_status st = species_args(c, y, "lf_get_mass_fractions")) return st;
   DeviceGuard g(c->cfg.device);
-  const size_t bytes = (size_t)c->mesh.nspecies * c->mesh.nx * c->mesh.ny * c->elem;
+  const size_t bytes = (size_t)c->nspecies * c->mesh.nx * c->mesh.ny * c->elem;
   void* dst = y;
   if (!on_device) {
     if (lf_status st = ensure_staging(c)) return st;
     dst = c->staging;
   }
-  cudaError_t e = c->elem == 8 ? lf::launch_cons_to_species<double>(c->mesh, static_cast<const double*>(c->U),
-                                                                   static_cast<double*>(dst), c->stream)
-                               : lf::launch_cons_to_species<float>(c->mesh, static_cast<const float*>(c->U),
-                                                                  static_cast<float*>(dst), c->stream);
+  cudaError_t e;
+  if (c->cfg.dim == 3)
+    e = c->elem == 8 ? lf::launch_cons_to_species3d(c->mesh3, static_cast<const double*>(c->U),
+                                                    static_cast<double*>(dst), c->stream)
+                     : lf::launch_cons_to_species3d(c->mesh3, static_cast<const float*>(c->U),
+                                                    static_cast<float*>(dst), c->stream);
+  else
+    e = c->elem == 8 ? lf::launch_cons_to_species<double>(c->mesh, static_cast<const double*>(c->U),
+                                                         static_cast<double*>(dst), c->stream)
+                     : lf::launch_cons_to_species<float>(c->mesh, static_cast<const float*>(c->U),
+                                                        static_cast<float*>(dst), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cons_to_species launch");
   if (!on_device) {
     LF_CUDA(c, cudaMemcpyAsync(y, dst, bytes, cudaMemcpyDeviceToHost, c->stream));

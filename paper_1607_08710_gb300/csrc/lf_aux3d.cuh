@@ -37,7 +37,7 @@ wave_speed3d_kernel(const Mesh3Desc m, const T* __restrict__ U, Scalars* sc) {
   }
 }
 
-// q: dense planes (rho, u, v, w, p), nx*ny*nz each; U: pitched state.
+// q: dense planes (rho, u, v, w, p, y_k), nx*ny*nz each; U: pitched state.
 template <typename T>
 __global__ void __launch_bounds__(AUX_THREADS)
 prim_to_cons3d_kernel(const Mesh3Desc m, const T* q, T* U) {
@@ -52,6 +52,7 @@ prim_to_cons3d_kernel(const Mesh3Desc m, const T* q, T* U) {
     U[2 * m.plane + idx] = rho * v;
     U[3 * m.plane + idx] = rho * w;
     U[4 * m.plane + idx] = p / gm1 + T(0.5) * rho * (u * u + v * v + w * w);
+    for (int s = 0; s < m.nspecies; ++s) U[(5 + s) * m.plane + idx] = rho * q[(5 + s) * n + k];
   }
 }
 
@@ -71,6 +72,32 @@ cons_to_prim3d_kernel(const Mesh3Desc m, const T* U, T* q) {
     q[2 * n + k] = v;
     q[3 * n + k] = w;
     q[4 * n + k] = gm1 * (E - T(0.5) * (mx * u + my * v + mz * w));
+    for (int s = 0; s < m.nspecies; ++s) q[(5 + s) * n + k] = U[(5 + s) * m.plane + idx] / rho;
+  }
+}
+
+// Species planes only: rho y_k = rho * y_k from dense fractions y, and back.
+template <typename T>
+__global__ void __launch_bounds__(AUX_THREADS)
+species_to_cons3d_kernel(const Mesh3Desc m, const T* y, T* U) {
+  const long long n = (long long)m.ny * m.nz * m.nx;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const long long r = k / m.nx, i = k - r * m.nx;
+    const long long idx = r * m.pitch + i;
+    const T rho = U[idx];
+    for (int s = 0; s < m.nspecies; ++s) U[(5 + s) * m.plane + idx] = rho * y[s * n + k];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(AUX_THREADS)
+cons_to_species3d_kernel(const Mesh3Desc m, const T* U, T* y) {
+  const long long n = (long long)m.ny * m.nz * m.nx;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const long long r = k / m.nx, i = k - r * m.nx;
+    const long long idx = r * m.pitch + i;
+    const T rho = U[idx];
+    for (int s = 0; s < m.nspecies; ++s) y[s * n + k] = U[(5 + s) * m.plane + idx] / rho;
   }
 }
 

@@ -15,6 +15,8 @@ struct lf_ctx {
   lf::MeshDesc mesh;          // 1D/2D mesh; for 3D the row view (ny*nz rows of nx cells)
   lf::Mesh3Desc mesh3{};      // 3D meshes only
   int nf = 4;                 // state planes: 4 (+1 in 3D) + nspecies
+  int nspecies = 0;           // transported mass fractions
+  int sp0 = 4;                // first species plane (4, or 5 in 3D)
   cudaStream_t stream = nullptr;
   size_t elem = 8;            // bytes per element
   void* U = nullptr;          // current state, nf pitched planes

@@ -50,10 +50,16 @@ cudaError_t launch_stage3d(int stage, const Mesh3Desc& m, const double* Uin, con
 // CFL wave-speed maximum of a freshly set state.
 cudaError_t launch_wave_speed3d(const Mesh3Desc& m, const float* U, Scalars* sc, cudaStream_t s);
 cudaError_t launch_wave_speed3d(const Mesh3Desc& m, const double* U, Scalars* sc, cudaStream_t s);
-// Primitive (rho, u, v, w, p) <-> conservative; q is dense (5 planes of nx*ny*nz).
+// Primitive (rho, u, v, w, p, y_k) <-> conservative; q is dense (5 + nspecies
+// planes of nx*ny*nz).
 cudaError_t launch_prim_to_cons3d(const Mesh3Desc& m, const float* q, float* U, cudaStream_t s);
 cudaError_t launch_prim_to_cons3d(const Mesh3Desc& m, const double* q, double* U, cudaStream_t s);
 cudaError_t launch_cons_to_prim3d(const Mesh3Desc& m, const float* U, float* q, cudaStream_t s);
 cudaError_t launch_cons_to_prim3d(const Mesh3Desc& m, const double* U, double* q, cudaStream_t s);
+// Species planes from dense mass fractions (rho y_k = rho * y_k) and back.
+cudaError_t launch_species_to_cons3d(const Mesh3Desc& m, const float* y, float* U, cudaStream_t s);
+cudaError_t launch_species_to_cons3d(const Mesh3Desc& m, const double* y, double* U, cudaStream_t s);
+cudaError_t launch_cons_to_species3d(const Mesh3Desc& m, const float* U, float* y, cudaStream_t s);
+cudaError_t launch_cons_to_species3d(const Mesh3Desc& m, const double* U, double* y, cudaStream_t s);
 
 }  // namespace lf

@@ -24,4 +24,14 @@ cudaError_t launch_cons_to_prim3d(const Mesh3Desc& m, const float* U, float* q, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_species_to_cons3d(const Mesh3Desc& m, const float* y, float* U, cudaStream_t s) {
+  species_to_cons3d_kernel<float><<<aux_blocks3(m), AUX_THREADS, 0, s>>>(m, y, U);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cons_to_species3d(const Mesh3Desc& m, const float* U, float* y, cudaStream_t s) {
+  cons_to_species3d_kernel<float><<<aux_blocks3(m), AUX_THREADS, 0, s>>>(m, U, y);
+  return cudaGetLastError();
+}
+
 }  // namespace lf

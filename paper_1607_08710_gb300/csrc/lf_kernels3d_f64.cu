@@ -24,4 +24,14 @@ cudaError_t launch_cons_to_prim3d(const Mesh3Desc& m, const double* U, double* q
   return cudaGetLastError();
 }
 
+cudaError_t launch_species_to_cons3d(const Mesh3Desc& m, const double* y, double* U, cudaStream_t s) {
+  species_to_cons3d_kernel<double><<<aux_blocks3(m), AUX_THREADS, 0, s>>>(m, y, U);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cons_to_species3d(const Mesh3Desc& m, const double* U, double* y, cudaStream_t s) {
+  cons_to_species3d_kernel<double><<<aux_blocks3(m), AUX_THREADS, 0, s>>>(m, U, y);
+  return cudaGetLastError();
+}
+
 }  // namespace lf

@@ -69,9 +69,11 @@ template <typename T>
 cudaError_t launch_sums(const MeshDesc& m, const T* U, double* partials, int nblocks, double* out,
                         cudaStream_t s) {
   sums_partial_kernel<T, 4><<<nblocks, AUX_THREADS, 0, s>>>(m, U, 0, partials);
+  // planes past the first four: species, or rho E and the species of a 3D state
   if (m.nspecies == 1) sums_partial_kernel<T, 1><<<nblocks, AUX_THREADS, 0, s>>>(m, U, 4, partials);
   else if (m.nspecies == 2) sums_partial_kernel<T, 2><<<nblocks, AUX_THREADS, 0, s>>>(m, U, 4, partials);
-  static_assert(MAX_SPECIES == 2, "species sums cover nspecies <= 2");
+  else if (m.nspecies == 3) sums_partial_kernel<T, 3><<<nblocks, AUX_THREADS, 0, s>>>(m, U, 4, partials);
+  static_assert(MAX_SPECIES == 2, "extra summed planes: nspecies <= 2, plus rho E in 3D");
   sums_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, 4 + m.nspecies, out);
   return cudaGetLastError();
 }

@@ -311,12 +311,14 @@ __device__ __forceinline__ void march_plane3(const Phys<V>& P, const Mesh3Desc& 
   }
 }
 
-template <typename T> struct MinBlocks3 { static constexpr int value = LF_3D_MIN_BLOCKS; };
-template <> struct MinBlocks3<double> { static constexpr int value = 1; };
+// FP32 gas dynamics: LF_3D_MIN_BLOCKS resident CTAs; with species the window
+// carries more fields and the allocator is asked for two; FP64 is uncapped.
+template <typename T, int NF> struct MinBlocks3 { static constexpr int value = NF == 5 ? LF_3D_MIN_BLOCKS : 2; };
+template <int NF> struct MinBlocks3<double, NF> { static constexpr int value = 1; };
 
 // Grid: (strips, ceil(ny / ROWS3), ceil(nz / TZ3)); ROWS3 warps per CTA.
 template <typename T, int LIM, int STAGE, int NF>
-__global__ void __launch_bounds__(ROWS3 * 32, (MinBlocks3<T>::value))
+__global__ void __launch_bounds__(ROWS3 * 32, (MinBlocks3<T, NF>::value))
 stage3d_kernel(const Mesh3Desc m, const T* __restrict__ Uin, const T* Un, T* out, Scalars* sc) {
   using V = typename StageShape<T>::V;
   constexpr int CPL = StageShape<T>::CPL;
@@ -444,14 +446,25 @@ cudaError_t launch_stage3d_lim(int stage, const Mesh3Desc& m, const T* Uin, cons
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
+template <typename T, int NF>
+cudaError_t launch_stage3d_nf(int stage, const Mesh3Desc& m, const T* Uin, const T* Un, T* out, Scalars* sc,
+                              cudaStream_t s) {
+  switch (m.limiter) {
+    case LIM_MINMOD: return launch_stage3d_lim<T, LIM_MINMOD, NF>(stage, m, Uin, Un, out, sc, s);
+    case LIM_SWEBY: return launch_stage3d_lim<T, LIM_SWEBY, NF>(stage, m, Uin, Un, out, sc, s);
+    default: return launch_stage3d_lim<T, LIM_VANLEER, NF>(stage, m, Uin, Un, out, sc, s);
+  }
+}
+
+// nspecies transported mass fractions: 5 + nspecies fields per cell.
 template <typename T>
 cudaError_t launch_stage3d_impl(int stage, const Mesh3Desc& m, const T* Uin, const T* Un, T* out, Scalars* sc,
                                 cudaStream_t s) {
-  if (m.nspecies != 0) return cudaErrorInvalidValue;
-  switch (m.limiter) {
-    case LIM_MINMOD: return launch_stage3d_lim<T, LIM_MINMOD, 5>(stage, m, Uin, Un, out, sc, s);
-    case LIM_SWEBY: return launch_stage3d_lim<T, LIM_SWEBY, 5>(stage, m, Uin, Un, out, sc, s);
-    default: return launch_stage3d_lim<T, LIM_VANLEER, 5>(stage, m, Uin, Un, out, sc, s);
+  switch (m.nspecies) {
+    case 0: return launch_stage3d_nf<T, 5>(stage, m, Uin, Un, out, sc, s);
+    case 1: return launch_stage3d_nf<T, 6>(stage, m, Uin, Un, out, sc, s);
+    case 2: return launch_stage3d_nf<T, 7>(stage, m, Uin, Un, out, sc, s);
+    default: return cudaErrorInvalidValue;
   }
 }
 

@@ -289,8 +289,7 @@ class LagrangeFlux:
 
     # -- species (Sec. 5) -------------------------------------------------
     def _species_buffer(self, a):
-        ny = self.cfg.ny if self.cfg.dim == 2 else 1
-        n = self.cfg.nspecies * self.cfg.nx * ny
+        n = self.cfg.nspecies * int(np.prod(self.cfg.shape))
         p, k = _ptr_and_kind(a)
         if int(np.prod(a.shape)) != n:
             raise ValueError(f"species buffer has {int(np.prod(a.shape))} elements, expected {n}")
@@ -299,12 +298,11 @@ class LagrangeFlux:
 
     def _species_out(self, out):
         if out is None:
-            ny = self.cfg.ny if self.cfg.dim == 2 else 1
-            out = np.empty((self.cfg.nspecies, ny, self.cfg.nx), dtype=self.cfg.np_dtype)
+            out = np.empty((self.cfg.nspecies,) + self.cfg.shape, dtype=self.cfg.np_dtype)
         return out
 
     def set_partial_densities(self, rho_y):
-        """rho_y: (nspecies, ny, nx) partial densities rho y_k."""
+        """rho_y: (nspecies,) + shape partial densities rho y_k."""
         p, k = self._species_buffer(rho_y)
         self._check(_lib.lf_set_partial_densities(self._h, p, k))
 
@@ -315,7 +313,7 @@ class LagrangeFlux:
         return out
 
     def set_mass_fractions(self, y):
-        """y: (nspecies, ny, nx) mass fractions; rho y_k uses the current density."""
+        """y: (nspecies,) + shape mass fractions; rho y_k uses the current density."""
         p, k = self._species_buffer(y)
         self._check(_lib.lf_set_mass_fractions(self._h, p, k))
 

@@ -77,7 +77,7 @@ def test_init_rejects_bad_config_without_gpu(lib, field, value):
     assert b"invalid configuration" in lib.lf_last_error(None)
 
 
-@pytest.mark.parametrize("field,value", [("zmax", 0.0), ("nz", 0), ("nspecies", 1)])
+@pytest.mark.parametrize("field,value", [("zmax", 0.0), ("nz", 0), ("nspecies", 3)])
 def test_init_rejects_bad_3d_config_without_gpu(lib, field, value):
     cfg = lib.Config(nx=8, ny=8, nz=8, dim=3).to_c()
     setattr(cfg, field, value)

@@ -202,3 +202,50 @@ def test_nonphysical_state_is_flagged_3d():
         s.run(max_steps=3)
     assert ei.value.status == 4  # LF_ERR_NONPHYSICAL
     s.close()
+
+
+def octant_with_species(nx, ny, nz, ns, seed):
+    base = inputs.octant(nx, ny, nz, seed=seed)
+    rng = np.random.default_rng(seed)
+    y = rng.uniform(0.0, 1.0, size=(ns, nz, ny, nx))
+    return inputs.with_species(base, y).stack()
+
+
+@pytest.mark.parametrize("ns", [1, 2])
+@pytest.mark.parametrize("time_order", [2, 3])
+def test_species_3d_fp64_against_oracle(ns, time_order):
+    q = octant_with_species(37, 14, 23, ns, seed=ns + 10 * time_order)
+    kw = dict(bc="periodic", limiter="vanleer", cfl=0.4, time_order=time_order, nspecies=ns)
+    ref = oracle3(q, 20, **kw)
+    U, _, _ = gpu3(q, "fp64", steps=20, **kw)
+    assert U.shape[0] == 5 + ns
+    assert_close(U, ref.U, FP64_TOL)
+
+
+def test_species_3d_fp32_and_invariants():
+    n = 40
+    base = inputs.shear_layer_3d(n, 24, 20, seed=3)
+    inside = np.abs(inputs.cell_centres(24)[None, :, None] - 0.5) < 0.25
+    y1 = np.broadcast_to(inside, base.shape).astype(np.float64)
+    q = inputs.with_species(base, np.stack([y1, 1.0 - y1])).stack()
+    kw = dict(bc="periodic", limiter="vanleer", cfl=0.45, nspecies=2)
+    ref = oracle3(q, 20, **kw)
+    U, _, _ = gpu3(q, "fp32", dts=ref.dts, **kw)
+    assert_close(U, ref.U, FP32_TOL, fp32=True)
+    # complementary fractions keep summing to one; species mass is conserved
+    s = LagrangeFlux(Config(nx=n, ny=24, nz=20, dim=3, **kw))
+    s.set_primitives(np.ascontiguousarray(q))
+    S0 = s.conservation_sums()
+    assert S0.shape == (7,)
+    s.run(max_steps=30)
+    S1 = s.conservation_sums()
+    for l in (0, 5, 6):
+        assert abs(S1[l] - S0[l]) <= 1e-12 * abs(S0[l])
+    rho_y = s.get_partial_densities()
+    assert rho_y.shape == (2, 20, 24, n)
+    U = s.get_conservative()
+    assert np.abs(rho_y[0] + rho_y[1] - U[0]).max() <= 1e-13 * np.abs(U[0]).max()
+    np.testing.assert_allclose(s.get_mass_fractions(), rho_y / U[0][None], rtol=1e-15, atol=0)
+    qb = s.get_primitives()
+    np.testing.assert_allclose(qb[5:], rho_y / U[0][None], rtol=1e-15, atol=0)
+    s.close()
