@@ -236,13 +236,16 @@ template <typename T, int CPL, int NF> struct Ring {
 };
 
 // Copies this lane's cells of (mapped) row offset `off` into buffer `buf`.
-template <typename T, int CPL, int NF>
+// INNER: the strip lies inside the row and vector accesses are allowed for
+// every lane (a warp-uniform property), so each lane issues one copy per
+// field; otherwise each lane takes the vector or the per-cell mapped path.
+template <typename T, int CPL, int NF, bool INNER = false>
 __device__ __forceinline__ void issue_row(T* buf, const T* const P[NF], const LaneCols<CPL>& L, int off, int lane) {
 #pragma unroll
   for (int k = 0; k < NF; ++k) {
     T* dst = buf + (k * 32 + lane) * CPL;
     const T* src = P[k] + off;
-    if (L.vec_ok) {
+    if (INNER || L.vec_ok) {
       cp_async<CPL * sizeof(T)>(dst, src + L.c0);
     } else {
 #pragma unroll
@@ -251,15 +254,16 @@ __device__ __forceinline__ void issue_row(T* buf, const T* const P[NF], const La
   }
 }
 
-// Same for the output cells only (row offset `off` inside the mesh).
-template <typename T, int CPL, int NF>
+// Same for the output cells only (row offset `off` inside the mesh).  INNER:
+// as issue_row; the halo lanes then copy their in-row cells too (never read).
+template <typename T, int CPL, int NF, bool INNER = false>
 __device__ __forceinline__ void issue_out_cells(T* buf, const T* const P[NF], const LaneCols<CPL>& L, int off,
                                                 int lane) {
 #pragma unroll
   for (int k = 0; k < NF; ++k) {
     T* dst = buf + (k * 32 + lane) * CPL;
     const T* src = P[k] + off + L.c0;
-    if (L.vec_ok) {
+    if (INNER || L.vec_ok) {
       cp_async<CPL * sizeof(T)>(dst, src);  // with vec_ok, all or none of the lane's cells are outputs
     } else {
 #pragma unroll
@@ -317,10 +321,10 @@ __device__ __forceinline__ int ring_in_plus(int si, int k) {
   return t >= RING_IN ? t - RING_IN : t;
 }
 
-template <typename T, typename V, int LIM, int STAGE, int CPL, int NF, int S>
+template <typename T, typename V, int LIM, int STAGE, int CPL, int NF, int S, bool INNER>
 __device__ __forceinline__ void march_row(const Phys<V>& P, const MeshDesc& m,
                                           const StageArgs<T, STAGE, CPL, NF>& A, const LaneCols<CPL>& L,
-                                          March<V, NF>& M, int lane, int r, int si, int jend, V ncx, V ncy,
+                                          March<V, NF>& M, int lane, int r, int si, V ncx, V ncy,
                                           T& smax, bool& bad) {
   constexpr int S1 = (S + 1) % 3, S2 = (S + 2) % 3;
   constexpr int ROW = Ring<T, CPL, NF>::ROW;
@@ -336,11 +340,11 @@ __device__ __forceinline__ void march_row(const Phys<V>& P, const MeshDesc& m,
   // end of the tile where they are not needed: the row index stays valid
   // (boundary-mapped, or clamped to the last row) and the target buffers
   // (rows r-1) are no longer read, so the branch-free row body costs two idle
-  // copies per tile.  strip_tile drains them before returning.
-  issue_row<T, CPL, NF>(A.ring_in + ring_in_plus(si, AHEAD_IN) * ROW, A.P, L,
-                        map_row(r + AHEAD_IN, m.ny, m.bc) * m.pitch, lane);
-  if (STAGE >= 1 && L.any_out)  // U^n row r+2 lives in register slot S2's ring buffer
-    issue_out_cells<T, CPL, NF>(A.ring_un + S2 * ROW, A.N, L, min(r + AHEAD_UN, m.ny - 1) * m.pitch, lane);
+  // copies per tile.  strip_tile_impl drains them before returning.
+  issue_row<T, CPL, NF, INNER>(A.ring_in + ring_in_plus(si, AHEAD_IN) * ROW, A.P, L,
+                               map_row(r + AHEAD_IN, m.ny, m.bc) * m.pitch, lane);
+  if (STAGE >= 1 && (INNER || L.any_out))  // U^n row r+2 lives in register slot S2's ring buffer
+    issue_out_cells<T, CPL, NF, INNER>(A.ring_un + S2 * ROW, A.N, L, min(r + AHEAD_UN, m.ny - 1) * m.pitch, lane);
   cp_commit();
   // y-slopes of row r+1 and the flux through face r+1/2
   {
@@ -370,14 +374,14 @@ __device__ __forceinline__ void march_row(const Phys<V>& P, const MeshDesc& m,
     W[k] = fma_(ncy, M.G[S1][k] - M.G[S][k], fma_(ncx, Fr[k] - Fl[k], base));
   }
   const int off = r * m.pitch;
-  if (L.vec_ok && L.any_out) {
+  if ((INNER || L.vec_ok) && L.any_out) {
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
       T v[CPL];
       split_lane(W[k], v);
       VecLoad<T, CPL>::store(A.O[k] + off + L.c0, v);
     }
-  } else if (!L.vec_ok) {
+  } else if (!INNER && !L.vec_ok) {
 #pragma unroll
     for (int j = 0; j < CPL; ++j)
       if (L.out[j])
@@ -399,10 +403,10 @@ __device__ __forceinline__ void march_row(const Phys<V>& P, const MeshDesc& m,
 // [j0, jend): the whole y-march, from the prologue to the last row.  The
 // warp's rings start empty and are left with no copy in flight.
 // STAGE 0: out = Uin - dt L(Uin).  STAGE 1: out = (Un + Uin)/2 - dt/2 L(Uin).
-template <typename T, typename V, int LIM, int STAGE, int CPL, int NF>
-__device__ __forceinline__ void strip_tile(const Phys<V>& P, const MeshDesc& m, const T* Uin, const T* Un, T* out,
-                                           int i0, int j0, int jend, T cx, T cy, T* ring_in, int lane, T& smax,
-                                           bool& bad) {
+template <typename T, typename V, int LIM, int STAGE, int CPL, int NF, bool INNER>
+__device__ __forceinline__ void strip_tile_impl(const Phys<V>& P, const MeshDesc& m, const T* Uin, const T* Un,
+                                                T* out, int i0, int j0, int jend, T cx, T cy, T* ring_in, int lane,
+                                                T& smax, bool& bad) {
   const LaneCols<CPL> L = lane_cols<CPL>(i0, lane, m.nx, m.bc, m.vec);
   constexpr int ROW = Ring<T, CPL, NF>::ROW;
   StageArgs<T, STAGE, CPL, NF> A;
@@ -422,12 +426,13 @@ __device__ __forceinline__ void strip_tile(const Phys<V>& P, const MeshDesc& m, 
   // and the flux through face j0-1/2 (slot 0).  Group 2 (input row j0+3, U^n
   // row j0+1) reuses row j0-2's buffer, so it is issued after that row is read.
   for (int row = j0 - 2; row <= j0 + 1; ++row)
-    issue_row<T, CPL, NF>(A.ring_in + ring_slot(row, j0, RING_IN) * ROW, A.P, L, map_row(row, m.ny, m.bc) * m.pitch,
-                      lane);
+    issue_row<T, CPL, NF, INNER>(A.ring_in + ring_slot(row, j0, RING_IN) * ROW, A.P, L,
+                                 map_row(row, m.ny, m.bc) * m.pitch, lane);
   cp_commit();
-  issue_row<T, CPL, NF>(A.ring_in + ring_slot(j0 + 2, j0, RING_IN) * ROW, A.P, L,
-                        map_row(j0 + 2, m.ny, m.bc) * m.pitch, lane);
-  if (STAGE >= 1 && L.any_out) issue_out_cells<T, CPL, NF>(A.ring_un + 0 * ROW, A.N, L, j0 * m.pitch, lane);
+  issue_row<T, CPL, NF, INNER>(A.ring_in + ring_slot(j0 + 2, j0, RING_IN) * ROW, A.P, L,
+                               map_row(j0 + 2, m.ny, m.bc) * m.pitch, lane);
+  if (STAGE >= 1 && (INNER || L.any_out))
+    issue_out_cells<T, CPL, NF, INNER>(A.ring_un + 0 * ROW, A.N, L, j0 * m.pitch, lane);
   cp_commit();
   cp_wait<1>();
   March<V, NF> M;
@@ -451,10 +456,10 @@ __device__ __forceinline__ void strip_tile(const Phys<V>& P, const MeshDesc& m, 
     lagrange_flux<V, 1, NF>(P, Lq, Rq, M.G[0]);
   }
   if (j0 + 1 < jend) {
-    issue_row<T, CPL, NF>(A.ring_in + ring_slot(j0 + 3, j0, RING_IN) * ROW, A.P, L,
-                          map_row(j0 + 3, m.ny, m.bc) * m.pitch, lane);
-    if (STAGE >= 1 && L.any_out)
-      issue_out_cells<T, CPL, NF>(A.ring_un + 1 * ROW, A.N, L, (j0 + 1) * m.pitch, lane);
+    issue_row<T, CPL, NF, INNER>(A.ring_in + ring_slot(j0 + 3, j0, RING_IN) * ROW, A.P, L,
+                                 map_row(j0 + 3, m.ny, m.bc) * m.pitch, lane);
+    if (STAGE >= 1 && (INNER || L.any_out))
+      issue_out_cells<T, CPL, NF, INNER>(A.ring_un + 1 * ROW, A.N, L, (j0 + 1) * m.pitch, lane);
   }
   cp_commit();
 
@@ -462,17 +467,34 @@ __device__ __forceinline__ void strip_tile(const Phys<V>& P, const MeshDesc& m, 
   // and dt/dy enter negated (fma(-c, d, b) == fma(c', d, b) with c' = -c)
   const V ncx = V(-cx), ncy = V(-cy);
   for (int r = j0, si = 0;;) {
-    march_row<T, V, LIM, STAGE, CPL, NF, 0>(P, m, A, L, M, lane, r, si, jend, ncx, ncy, smax, bad);
+    march_row<T, V, LIM, STAGE, CPL, NF, 0, INNER>(P, m, A, L, M, lane, r, si, ncx, ncy, smax, bad);
     if (++r >= jend) break;
     si = ring_in_plus(si, 1);
-    march_row<T, V, LIM, STAGE, CPL, NF, 1>(P, m, A, L, M, lane, r, si, jend, ncx, ncy, smax, bad);
+    march_row<T, V, LIM, STAGE, CPL, NF, 1, INNER>(P, m, A, L, M, lane, r, si, ncx, ncy, smax, bad);
     if (++r >= jend) break;
     si = ring_in_plus(si, 1);
-    march_row<T, V, LIM, STAGE, CPL, NF, 2>(P, m, A, L, M, lane, r, si, jend, ncx, ncy, smax, bad);
+    march_row<T, V, LIM, STAGE, CPL, NF, 2, INNER>(P, m, A, L, M, lane, r, si, ncx, ncy, smax, bad);
     if (++r >= jend) break;
     si = ring_in_plus(si, 1);
   }
   cp_wait_all();
+}
+
+// A strip whose 32*CPL columns all lie inside the row, with vector accesses
+// allowed, runs the march without per-lane copy or store choices (decided
+// once per warp: i0 is warp-uniform); edge strips take the mapped path.  Both
+// do the same arithmetic, so results do not depend on which one ran.
+template <typename T, typename V, int LIM, int STAGE, int CPL, int NF>
+__device__ __forceinline__ void strip_tile(const Phys<V>& P, const MeshDesc& m, const T* Uin, const T* Un, T* out,
+                                           int i0, int j0, int jend, T cx, T cy, T* ring_in, int lane, T& smax,
+                                           bool& bad) {
+  const bool inner = (CPL == 1 || m.vec) && i0 - 2 >= 0 && i0 - 2 + 32 * CPL <= m.nx;
+  if (inner)
+    strip_tile_impl<T, V, LIM, STAGE, CPL, NF, true>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring_in, lane, smax,
+                                                      bad);
+  else
+    strip_tile_impl<T, V, LIM, STAGE, CPL, NF, false>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring_in, lane, smax,
+                                                       bad);
 }
 
 // One mesh: a 2D grid of (strips / STAGE_WARPS) x (row tiles) CTAs.
@@ -557,8 +579,11 @@ batch_stage_kernel(const BatchDesc b, const T* Uin, const T* Un, T* out, Scalars
     const T cx = T(hs * dtd * m.rdx), cy = T(hs * dtd * m.rdy);
     T smax = T(0);
     bool bad = false;
-    strip_tile<T, V, LIM, STAGE, CPL, 4>(P, m, Uin + pd.off, Un + pd.off, out + pd.off, un.i0, un.j0, un.jend, cx,
-                                         cy, ring, lane, smax, bad);
+    // one march body: warps move between small meshes whose strips are
+    // mostly edge strips, and a second (inner) copy of the march measured
+    // slower here through instruction-cache pressure
+    strip_tile_impl<T, V, LIM, STAGE, CPL, 4, false>(P, m, Uin + pd.off, Un + pd.off, out + pd.off, un.i0, un.j0,
+                                                     un.jend, cx, cy, ring, lane, smax, bad);
     if (StageCoef<STAGE>::speed) publish_speed(scp, scp->parity ^ 1, smax, bad);
   }
 }
