@@ -4,6 +4,7 @@
 
 #include "lf_adjoint.cuh"
 #include "lf_aux.cuh"
+#include "lf_batch_stage.cuh"
 #include "lf_stage.cuh"
 
 namespace lf {

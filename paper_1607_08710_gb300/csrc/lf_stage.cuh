@@ -55,6 +55,14 @@ template <int CPL> struct StripGeom {
   static constexpr int OUT = 32 * CPL - 4;  // output columns per warp
 };
 
+// A strip whose 32*CPL columns [i0-2, i0-2+32*CPL) all lie inside the row,
+// with vector accesses allowed (FP32 pairs need the even row pitch and the
+// aligned planes that m.vec certifies).  Uniform over a warp.
+template <int CPL>
+__device__ __forceinline__ bool inner_strip(const MeshDesc& m, int i0) {
+  return (CPL == 1 || m.vec) && i0 - 2 >= 0 && i0 - 2 + 32 * CPL <= m.nx;
+}
+
 // Rows are uniform across a warp; wrap or clamp without an integer division.
 __device__ __forceinline__ int map_row(int r, int n, int bc) {
   if (bc == BC_PERIODIC) {
@@ -235,17 +243,27 @@ template <typename T, int CPL, int NF> struct Ring {
   static __host__ __device__ constexpr size_t warp_bytes(int stage) { return (size_t)buffers(stage) * ROW * sizeof(T); }
 };
 
+// How a strip's march makes its copies and stores.  An inner strip lies
+// inside the row with vector accesses allowed for every lane (a warp-uniform
+// property), so each lane issues one copy per field and row; other strips
+// choose per lane between the vector and the per-cell boundary-mapped path.
+//   MARCH_MAPPED: per-lane choice (any strip)
+//   MARCH_INNER:  the strip is inner (compiled without the per-lane choice)
+enum { MARCH_MAPPED = 0, MARCH_INNER = 1 };
+
 // Copies this lane's cells of (mapped) row offset `off` into buffer `buf`.
-// INNER: the strip lies inside the row and vector accesses are allowed for
-// every lane (a warp-uniform property), so each lane issues one copy per
-// field; otherwise each lane takes the vector or the per-cell mapped path.
-template <typename T, int CPL, int NF, bool INNER = false>
+template <typename T, int CPL, int NF, int MODE = MARCH_MAPPED>
 __device__ __forceinline__ void issue_row(T* buf, const T* const P[NF], const LaneCols<CPL>& L, int off, int lane) {
+  if (MODE == MARCH_INNER) {
+#pragma unroll
+    for (int k = 0; k < NF; ++k) cp_async<CPL * sizeof(T)>(buf + (k * 32 + lane) * CPL, P[k] + off + L.c0);
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < NF; ++k) {
     T* dst = buf + (k * 32 + lane) * CPL;
     const T* src = P[k] + off;
-    if (INNER || L.vec_ok) {
+    if (L.vec_ok) {
       cp_async<CPL * sizeof(T)>(dst, src + L.c0);
     } else {
 #pragma unroll
@@ -254,16 +272,22 @@ __device__ __forceinline__ void issue_row(T* buf, const T* const P[NF], const La
   }
 }
 
-// Same for the output cells only (row offset `off` inside the mesh).  INNER:
-// as issue_row; the halo lanes then copy their in-row cells too (never read).
-template <typename T, int CPL, int NF, bool INNER = false>
+// Same for the output cells only (row offset `off` inside the mesh).  In an
+// inner strip the halo lanes copy their in-row cells too (never read).
+template <typename T, int CPL, int NF, int MODE = MARCH_MAPPED>
 __device__ __forceinline__ void issue_out_cells(T* buf, const T* const P[NF], const LaneCols<CPL>& L, int off,
                                                 int lane) {
+  if (MODE == MARCH_INNER) {
+#pragma unroll
+    for (int k = 0; k < NF; ++k) cp_async<CPL * sizeof(T)>(buf + (k * 32 + lane) * CPL, P[k] + off + L.c0);
+    return;
+  }
+  if (!L.any_out) return;
 #pragma unroll
   for (int k = 0; k < NF; ++k) {
     T* dst = buf + (k * 32 + lane) * CPL;
     const T* src = P[k] + off + L.c0;
-    if (INNER || L.vec_ok) {
+    if (L.vec_ok) {
       cp_async<CPL * sizeof(T)>(dst, src);  // with vec_ok, all or none of the lane's cells are outputs
     } else {
 #pragma unroll
@@ -321,7 +345,7 @@ __device__ __forceinline__ int ring_in_plus(int si, int k) {
   return t >= RING_IN ? t - RING_IN : t;
 }
 
-template <typename T, typename V, int LIM, int STAGE, int CPL, int NF, int S, bool INNER>
+template <typename T, typename V, int LIM, int STAGE, int CPL, int NF, int S, int MODE>
 __device__ __forceinline__ void march_row(const Phys<V>& P, const MeshDesc& m,
                                           const StageArgs<T, STAGE, CPL, NF>& A, const LaneCols<CPL>& L,
                                           March<V, NF>& M, int lane, int r, int si, V ncx, V ncy,
@@ -341,10 +365,10 @@ __device__ __forceinline__ void march_row(const Phys<V>& P, const MeshDesc& m,
   // (boundary-mapped, or clamped to the last row) and the target buffers
   // (rows r-1) are no longer read, so the branch-free row body costs two idle
   // copies per tile.  strip_tile_impl drains them before returning.
-  issue_row<T, CPL, NF, INNER>(A.ring_in + ring_in_plus(si, AHEAD_IN) * ROW, A.P, L,
-                               map_row(r + AHEAD_IN, m.ny, m.bc) * m.pitch, lane);
-  if (STAGE >= 1 && (INNER || L.any_out))  // U^n row r+2 lives in register slot S2's ring buffer
-    issue_out_cells<T, CPL, NF, INNER>(A.ring_un + S2 * ROW, A.N, L, min(r + AHEAD_UN, m.ny - 1) * m.pitch, lane);
+  issue_row<T, CPL, NF, MODE>(A.ring_in + ring_in_plus(si, AHEAD_IN) * ROW, A.P, L,
+                              map_row(r + AHEAD_IN, m.ny, m.bc) * m.pitch, lane);
+  if (STAGE >= 1)  // U^n row r+2 lives in register slot S2's ring buffer
+    issue_out_cells<T, CPL, NF, MODE>(A.ring_un + S2 * ROW, A.N, L, min(r + AHEAD_UN, m.ny - 1) * m.pitch, lane);
   cp_commit();
   // y-slopes of row r+1 and the flux through face r+1/2
   {
@@ -374,14 +398,14 @@ __device__ __forceinline__ void march_row(const Phys<V>& P, const MeshDesc& m,
     W[k] = fma_(ncy, M.G[S1][k] - M.G[S][k], fma_(ncx, Fr[k] - Fl[k], base));
   }
   const int off = r * m.pitch;
-  if ((INNER || L.vec_ok) && L.any_out) {
+  if ((MODE == MARCH_INNER || L.vec_ok) && L.any_out) {
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
       T v[CPL];
       split_lane(W[k], v);
       VecLoad<T, CPL>::store(A.O[k] + off + L.c0, v);
     }
-  } else if (!INNER && !L.vec_ok) {
+  } else if (MODE != MARCH_INNER && !L.vec_ok) {
 #pragma unroll
     for (int j = 0; j < CPL; ++j)
       if (L.out[j])
@@ -403,7 +427,7 @@ __device__ __forceinline__ void march_row(const Phys<V>& P, const MeshDesc& m,
 // [j0, jend): the whole y-march, from the prologue to the last row.  The
 // warp's rings start empty and are left with no copy in flight.
 // STAGE 0: out = Uin - dt L(Uin).  STAGE 1: out = (Un + Uin)/2 - dt/2 L(Uin).
-template <typename T, typename V, int LIM, int STAGE, int CPL, int NF, bool INNER>
+template <typename T, typename V, int LIM, int STAGE, int CPL, int NF, int MODE>
 __device__ __forceinline__ void strip_tile_impl(const Phys<V>& P, const MeshDesc& m, const T* Uin, const T* Un,
                                                 T* out, int i0, int j0, int jend, T cx, T cy, T* ring_in, int lane,
                                                 T& smax, bool& bad) {
@@ -426,13 +450,12 @@ __device__ __forceinline__ void strip_tile_impl(const Phys<V>& P, const MeshDesc
   // and the flux through face j0-1/2 (slot 0).  Group 2 (input row j0+3, U^n
   // row j0+1) reuses row j0-2's buffer, so it is issued after that row is read.
   for (int row = j0 - 2; row <= j0 + 1; ++row)
-    issue_row<T, CPL, NF, INNER>(A.ring_in + ring_slot(row, j0, RING_IN) * ROW, A.P, L,
-                                 map_row(row, m.ny, m.bc) * m.pitch, lane);
+    issue_row<T, CPL, NF, MODE>(A.ring_in + ring_slot(row, j0, RING_IN) * ROW, A.P, L,
+                                map_row(row, m.ny, m.bc) * m.pitch, lane);
   cp_commit();
-  issue_row<T, CPL, NF, INNER>(A.ring_in + ring_slot(j0 + 2, j0, RING_IN) * ROW, A.P, L,
-                               map_row(j0 + 2, m.ny, m.bc) * m.pitch, lane);
-  if (STAGE >= 1 && (INNER || L.any_out))
-    issue_out_cells<T, CPL, NF, INNER>(A.ring_un + 0 * ROW, A.N, L, j0 * m.pitch, lane);
+  issue_row<T, CPL, NF, MODE>(A.ring_in + ring_slot(j0 + 2, j0, RING_IN) * ROW, A.P, L,
+                              map_row(j0 + 2, m.ny, m.bc) * m.pitch, lane);
+  if (STAGE >= 1) issue_out_cells<T, CPL, NF, MODE>(A.ring_un + 0 * ROW, A.N, L, j0 * m.pitch, lane);
   cp_commit();
   cp_wait<1>();
   March<V, NF> M;
@@ -456,10 +479,10 @@ __device__ __forceinline__ void strip_tile_impl(const Phys<V>& P, const MeshDesc
     lagrange_flux<V, 1, NF>(P, Lq, Rq, M.G[0]);
   }
   if (j0 + 1 < jend) {
-    issue_row<T, CPL, NF, INNER>(A.ring_in + ring_slot(j0 + 3, j0, RING_IN) * ROW, A.P, L,
-                                 map_row(j0 + 3, m.ny, m.bc) * m.pitch, lane);
-    if (STAGE >= 1 && (INNER || L.any_out))
-      issue_out_cells<T, CPL, NF, INNER>(A.ring_un + 1 * ROW, A.N, L, (j0 + 1) * m.pitch, lane);
+    issue_row<T, CPL, NF, MODE>(A.ring_in + ring_slot(j0 + 3, j0, RING_IN) * ROW, A.P, L,
+                                map_row(j0 + 3, m.ny, m.bc) * m.pitch, lane);
+    if (STAGE >= 1)
+      issue_out_cells<T, CPL, NF, MODE>(A.ring_un + 1 * ROW, A.N, L, (j0 + 1) * m.pitch, lane);
   }
   cp_commit();
 
@@ -467,13 +490,13 @@ __device__ __forceinline__ void strip_tile_impl(const Phys<V>& P, const MeshDesc
   // and dt/dy enter negated (fma(-c, d, b) == fma(c', d, b) with c' = -c)
   const V ncx = V(-cx), ncy = V(-cy);
   for (int r = j0, si = 0;;) {
-    march_row<T, V, LIM, STAGE, CPL, NF, 0, INNER>(P, m, A, L, M, lane, r, si, ncx, ncy, smax, bad);
+    march_row<T, V, LIM, STAGE, CPL, NF, 0, MODE>(P, m, A, L, M, lane, r, si, ncx, ncy, smax, bad);
     if (++r >= jend) break;
     si = ring_in_plus(si, 1);
-    march_row<T, V, LIM, STAGE, CPL, NF, 1, INNER>(P, m, A, L, M, lane, r, si, ncx, ncy, smax, bad);
+    march_row<T, V, LIM, STAGE, CPL, NF, 1, MODE>(P, m, A, L, M, lane, r, si, ncx, ncy, smax, bad);
     if (++r >= jend) break;
     si = ring_in_plus(si, 1);
-    march_row<T, V, LIM, STAGE, CPL, NF, 2, INNER>(P, m, A, L, M, lane, r, si, ncx, ncy, smax, bad);
+    march_row<T, V, LIM, STAGE, CPL, NF, 2, MODE>(P, m, A, L, M, lane, r, si, ncx, ncy, smax, bad);
     if (++r >= jend) break;
     si = ring_in_plus(si, 1);
   }
@@ -488,13 +511,12 @@ template <typename T, typename V, int LIM, int STAGE, int CPL, int NF>
 __device__ __forceinline__ void strip_tile(const Phys<V>& P, const MeshDesc& m, const T* Uin, const T* Un, T* out,
                                            int i0, int j0, int jend, T cx, T cy, T* ring_in, int lane, T& smax,
                                            bool& bad) {
-  const bool inner = (CPL == 1 || m.vec) && i0 - 2 >= 0 && i0 - 2 + 32 * CPL <= m.nx;
-  if (inner)
-    strip_tile_impl<T, V, LIM, STAGE, CPL, NF, true>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring_in, lane, smax,
-                                                      bad);
+  if (inner_strip<CPL>(m, i0))
+    strip_tile_impl<T, V, LIM, STAGE, CPL, NF, MARCH_INNER>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring_in, lane,
+                                                            smax, bad);
   else
-    strip_tile_impl<T, V, LIM, STAGE, CPL, NF, false>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring_in, lane, smax,
-                                                       bad);
+    strip_tile_impl<T, V, LIM, STAGE, CPL, NF, MARCH_MAPPED>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring_in, lane,
+                                                             smax, bad);
 }
 
 // One mesh: a 2D grid of (strips / STAGE_WARPS) x (row tiles) CTAs.
@@ -537,76 +559,6 @@ stage2d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
   bool bad = false;
   strip_tile<T, V, LIM, STAGE, CPL, NF>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring, lane, smax, bad);
   if (StageCoef<STAGE>::speed) publish_speed(sc, wpar, smax, bad);
-}
-
-// Many meshes: a persistent grid whose warps pull work units (problem, strip,
-// row tile) from an atomic counter until the list is exhausted.  Each problem
-// uses its own dt, and its corrector units feed its own wave-speed maximum.
-// (Gas dynamics only: NF = 4.)
-#ifndef LF_BATCH_MIN_BLOCKS
-#define LF_BATCH_MIN_BLOCKS (16 / LF_STAGE_WARPS)
-#endif
-template <typename T> struct BatchMinBlocks { static constexpr int value = LF_BATCH_MIN_BLOCKS; };
-template <> struct BatchMinBlocks<double> { static constexpr int value = 1; };
-
-template <typename T, int LIM, int STAGE, int CPL>
-__global__ void __launch_bounds__(STAGE_WARPS * 32, (BatchMinBlocks<T>::value))
-batch_stage_kernel(const BatchDesc b, const T* Uin, const T* Un, T* out, Scalars* sc, int* counter) {
-  extern __shared__ __align__(16) unsigned char lf_stage_smem[];
-  constexpr unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T* ring = reinterpret_cast<T*>(lf_stage_smem + warp * Ring<T, CPL, 4>::warp_bytes(STAGE));
-  for (;;) {
-    int u = 0;
-    if (lane == 0) u = atomicAdd(counter, 1);
-    u = __shfl_sync(FULL, u, 0);
-    if (u >= b.nunits) break;
-    const Unit un = b.units[u];
-    const ProbDesc pd = b.probs[un.p];
-    Scalars* scp = sc + un.p;
-    const double dtd = scp->dt;
-    if (!(dtd > 0.0)) continue;  // problem finished (t_end reached) or flagged
-    MeshDesc m = b.common;
-    m.nx = pd.nx;
-    m.ny = pd.ny;
-    m.pitch = pd.pitch;
-    m.plane = pd.plane;
-    m.rdx = pd.rdx;
-    m.rdy = pd.rdy;
-    using V = typename StageShape<T>::V;
-    const Phys<V> P(m);
-    const double hs = StageCoef<STAGE>::beta;
-    const T cx = T(hs * dtd * m.rdx), cy = T(hs * dtd * m.rdy);
-    T smax = T(0);
-    bool bad = false;
-    // one march body: warps move between small meshes whose strips are
-    // mostly edge strips, and a second (inner) copy of the march measured
-    // slower here through instruction-cache pressure
-    strip_tile_impl<T, V, LIM, STAGE, CPL, 4, false>(P, m, Uin + pd.off, Un + pd.off, out + pd.off, un.i0, un.j0,
-                                                     un.jend, cx, cy, ring, lane, smax, bad);
-    if (StageCoef<STAGE>::speed) publish_speed(scp, scp->parity ^ 1, smax, bad);
-  }
-}
-
-template <typename T, int LIM>
-cudaError_t launch_batch_stage_lim(int stage, const BatchDesc& b, const T* Uin, const T* Un, T* out, Scalars* sc,
-                                   int* counter, cudaStream_t s) {
-  constexpr int CPL = StageShape<T>::CPL;
-  const size_t smem = STAGE_WARPS * Ring<T, CPL, 4>::warp_bytes(stage);
-  if (stage == 0) batch_stage_kernel<T, LIM, 0, CPL><<<b.grid, STAGE_WARPS * 32, smem, s>>>(b, Uin, Un, out, sc, counter);
-  else batch_stage_kernel<T, LIM, 1, CPL><<<b.grid, STAGE_WARPS * 32, smem, s>>>(b, Uin, Un, out, sc, counter);
-  return cudaGetLastError();
-}
-
-template <typename T, int LIM>
-int batch_blocks_lim(int stage) {
-  constexpr int CPL = StageShape<T>::CPL;
-  const size_t smem = STAGE_WARPS * Ring<T, CPL, 4>::warp_bytes(stage);
-  int nb = 0;
-  cudaError_t e = stage == 0
-      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_stage_kernel<T, LIM, 0, CPL>, STAGE_WARPS * 32, smem)
-      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_stage_kernel<T, LIM, 1, CPL>, STAGE_WARPS * 32, smem);
-  return e == cudaSuccess ? nb : 0;
 }
 
 // 1D: one row, no y-terms.
@@ -688,25 +640,6 @@ cudaError_t launch_stage_lim(int stage, const MeshDesc& m, const T* Uin, const T
     }
   }
   return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_batch_stage_impl(int stage, const BatchDesc& b, const T* Uin, const T* Un, T* out, Scalars* sc,
-                                    int* counter, cudaStream_t s) {
-  switch (b.common.limiter) {
-    case LIM_MINMOD: return launch_batch_stage_lim<T, LIM_MINMOD>(stage, b, Uin, Un, out, sc, counter, s);
-    case LIM_SWEBY: return launch_batch_stage_lim<T, LIM_SWEBY>(stage, b, Uin, Un, out, sc, counter, s);
-    default: return launch_batch_stage_lim<T, LIM_VANLEER>(stage, b, Uin, Un, out, sc, counter, s);
-  }
-}
-
-template <typename T>
-int batch_blocks_impl(int stage, int limiter) {
-  switch (limiter) {
-    case LIM_MINMOD: return batch_blocks_lim<T, LIM_MINMOD>(stage);
-    case LIM_SWEBY: return batch_blocks_lim<T, LIM_SWEBY>(stage);
-    default: return batch_blocks_lim<T, LIM_VANLEER>(stage);
-  }
 }
 
 // Stage launch for meshes with NF fields per cell.

@@ -126,6 +126,7 @@ struct Args3 {
   long long own_off;   // element offset of this warp's (mapped) row in a plane of rows
   long long halo_off;  // the same for the halo row this warp copies (warps 0-3)
   int halo_rr;         // that halo row's index in the CTA's rows (-1: none)
+  bool inner;          // the strip lies inside the rows: one vector copy per lane and row (CTA-uniform)
 };
 
 // This warp's copies of input plane `k` into its ring slot: its own row and,
@@ -137,11 +138,22 @@ __device__ __forceinline__ void issue_plane3(const Mesh3Desc& m, const Args3<T, 
   const long long zoff = (long long)map_row(k, m.nz, m.bc) * m.ny * m.pitch;
   T* slot = A.ring + ((k - A.k0 + 4) & 3) * SM::PLANE_IN + CPL * lane;
   const T* src = A.Uin + zoff + A.own_off;
+  const T* hsrc = A.Uin + zoff + A.halo_off;
+  if (A.inner) {  // a uniform branch around all copies of the plane
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+      cp_async<CPL * sizeof(T)>(slot + (warp + 2) * SM::ROWSEG + f * 32 * CPL, src + f * m.plane + L.c0);
+    if (A.halo_rr >= 0) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        cp_async<CPL * sizeof(T)>(slot + A.halo_rr * SM::ROWSEG + f * 32 * CPL, hsrc + f * m.plane + L.c0);
+    }
+    return;
+  }
 #pragma unroll
   for (int f = 0; f < NF; ++f)
     copy_cells<T, CPL>(slot + (warp + 2) * SM::ROWSEG + f * 32 * CPL, src + f * m.plane, L);
   if (A.halo_rr >= 0) {
-    const T* hsrc = A.Uin + zoff + A.halo_off;
 #pragma unroll
     for (int f = 0; f < NF; ++f)
       copy_cells<T, CPL>(slot + A.halo_rr * SM::ROWSEG + f * 32 * CPL, hsrc + f * m.plane, L);
@@ -153,12 +165,19 @@ template <typename T, int STAGE, int CPL, int NF>
 __device__ __forceinline__ void issue_un3(const Mesh3Desc& m, const Args3<T, STAGE, NF>& A, const LaneCols<CPL>& L,
                                           int k, int warp, int lane, int jrow) {
   using SM = Smem3<T, CPL, NF>;
-  if (STAGE == 0 || !L.any_out || jrow >= m.ny) return;
+  if (STAGE == 0 || jrow >= m.ny) return;  // uniform over the warp
   const int zc = min(k, m.nz - 1);
   T* seg = A.unr + ((k - A.k0) & 1) * SM::PLANE_UN + warp * SM::ROWSEG;
+  const T* row = A.Un + ((long long)zc * m.ny + jrow) * m.pitch + L.c0;
+  if (A.inner) {  // halo lanes copy their in-row cells too (never read)
+#pragma unroll
+    for (int f = 0; f < NF; ++f) cp_async<CPL * sizeof(T)>(seg + f * 32 * CPL + CPL * lane, row + f * m.plane);
+    return;
+  }
+  if (!L.any_out) return;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    const T* src = A.Un + f * m.plane + ((long long)zc * m.ny + jrow) * m.pitch + L.c0;
+    const T* src = row + f * m.plane;
     T* dst = seg + f * 32 * CPL + CPL * lane;
     if (L.vec_ok) {
       cp_async<CPL * sizeof(T)>(dst, src);
@@ -345,6 +364,7 @@ stage3d_kernel(const Mesh3Desc m, const T* __restrict__ Uin, const T* Un, T* out
   A.own_off = (long long)map_row(jrow, m.ny, m.bc) * m.pitch;
   A.halo_rr = warp < HALO3 ? (warp < 2 ? warp : ROWS3 + warp) : -1;
   A.halo_off = A.halo_rr >= 0 ? (long long)map_row(j0 - 2 + A.halo_rr, m.ny, m.bc) * m.pitch : 0;
+  A.inner = i0 - 2 >= 0 && i0 - 2 + 32 * CPL <= m.nx;
   const LaneCols<CPL> L = lane_cols<CPL>(i0, lane, m.nx, m.bc, 1);
   const double hs = StageCoef<STAGE>::beta;
   const V ncx = V(-T(hs * dtd * m.rdx)), ncy = V(-T(hs * dtd * m.rdy)), ncz = V(-T(hs * dtd * m.rdz));
