@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--steps3d", type=int, default=50)
     ap.add_argument("--batch-problems", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=300)
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-size", type=int, default=512)
+    ap.add_argument("--adjoint-steps", type=int, default=256)
     return ap.parse_args()
 
 
@@ -309,6 +312,72 @@ def run_batched(args, dist, dev):
             "workload": "four-quadrant Riemann problems, sides log-uniform in [64, 1024], seeds 0..P-1"}
 
 
+def run_adjoint(args, dev):
+    """Gradient of J = sum (rho(T) - rho_target)^2 with respect to the initial
+    (rho, u, v, p), 512 x 512 periodic Kelvin-Helmholtz layer, 256 steps at
+    CFL 0.4, van Leer, FP64 and FP32: the checkpointed forward sweep
+    (lf_adjoint_forward) and the reverse sweep (lf_adjoint_backward), each
+    timed with CUDA events, against a plain forward run of the same steps.
+    rho_target is rho(T) of a run from the same layer with a seeded smooth
+    density perturbation (not timed)."""
+    import torch
+
+    from paper_1607_08710_gb300 import inputs
+    from paper_1607_08710_gb300.lagflux import Config, LagrangeFlux
+
+    n, nsteps = args.adjoint_size, args.adjoint_steps
+    cells = n * n
+    q0 = inputs.kelvin_helmholtz(n, n, seed=0).stack()
+    qt = q0.copy()
+    qt[0] += 1e-2 * inputs.smooth_perturbation(n, n, seed=98)
+    res = {"workload": f"periodic Kelvin-Helmholtz shear layer {n}x{n}, {nsteps} steps at CFL 0.4, "
+                       "J = sum (rho(T) - rho_target)^2, gradient in (rho, u, v, p)(0)",
+           "unit": METRIC, "steps": nsteps, "checkpoints": "every ceil(sqrt(N)) steps, segments recomputed once"}
+    for prec, tdt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        kw = dict(nx=n, ny=n, precision=prec, limiter="vanleer", bc="periodic", cfl=0.4)
+        s = LagrangeFlux(Config(**kw))
+        q = torch.from_numpy(qt).to(dev, tdt)
+        s.set_primitive(q[0], q[1], q[2], q[3])
+        s.run(max_steps=nsteps)
+        UT = torch.empty((4, n, n), dtype=tdt, device=dev)
+        s.get_state(UT)
+        rho_target = UT[0].clone()
+        q = torch.from_numpy(q0).to(dev, tdt)
+        lam = torch.zeros((4, n, n), dtype=tdt, device=dev)
+        gq = torch.empty((4, n, n), dtype=tdt, device=dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        for rep in range(2):  # the first pass warms up; the second is timed
+            s.set_primitive(q[0], q[1], q[2], q[3])
+            torch.cuda.synchronize()
+            ev[0].record()
+            s.run(max_steps=nsteps)
+            ev[1].record()
+            s.set_primitive(q[0], q[1], q[2], q[3])
+            torch.cuda.synchronize()
+            ev[2].record()
+            s.adjoint_forward(nsteps)
+            ev[3].record()
+            s.get_state(UT)
+            lam[0] = 2.0 * (UT[0] - rho_target)
+            torch.cuda.synchronize()
+            e_b0 = torch.cuda.Event(enable_timing=True)
+            e_b0.record()
+            s.adjoint_backward(lam, grad_q0=gq)
+            ev[4].record()
+            torch.cuda.synchronize()
+        t_plain = ev[0].elapsed_time(ev[1]) / 1e3
+        t_fwd = ev[2].elapsed_time(ev[3]) / 1e3
+        t_bwd = e_b0.elapsed_time(ev[4]) / 1e3
+        assert bool(torch.isfinite(gq).all())
+        s.close()
+        res[prec] = {"value": cells * nsteps / (t_fwd + t_bwd), "forward_ms": 1e3 * t_fwd,
+                     "backward_ms": 1e3 * t_bwd, "plain_forward_ms": 1e3 * t_plain,
+                     "gradient_over_forward": (t_fwd + t_bwd) / t_plain}
+        del q, UT, lam, gq
+        torch.cuda.empty_cache()
+    return res
+
+
 def run_ours(args, dist):
     import torch
 
@@ -534,6 +603,10 @@ def run_ours(args, dist):
                          "algorithmic_bytes_per_cell": byts[sk] // cells3},
             "workload": f"periodic 3D shear layer {n3}^3 (Kelvin-Helmholtz layer, perturbation x cos(2 pi z))"}
         torch.cuda.empty_cache()
+
+    # discrete adjoint: gradient of a final-time objective through the checkpointed step loop
+    if not args.no_adjoint and dist.rank == 0:
+        out["adjoint"] = run_adjoint(args, dev)
 
     # batched: 512 seeded uneven meshes, one persistent launch per stage, graph of the step loop
     if not args.no_batch:

@@ -107,7 +107,10 @@ typedef struct lf_config {
   double cfl;        /* CFL number, 0 < cfl <= 1 */
   double beta;       /* Sweby coefficient, 1 <= beta <= 2 (LF_LIMITER_SWEBY) */
   int32_t nz;        /* cells in z (dim == 3); 0 or 1 otherwise */
-  int32_t reserved;  /* must be 0 */
+  int32_t tile_rows; /* rows per tile of the 2D stage kernels, 1 .. 4096; 0: chosen
+                        by lf_init from the mesh size and the GPU's SM count (64-row
+                        tiles unless that leaves the GPU short of work).  A launch
+                        shape only: results do not depend on it, bit for bit. */
   double zmin, zmax; /* domain in z (dim == 3) */
 } lf_config;
 
@@ -192,6 +195,22 @@ lf_status lf_conservation_sums(lf_ctx* ctx, double* out);
 
 /* Waits for the context's stream and reports any device-side error flag. */
 lf_status lf_sync(lf_ctx* ctx);
+
+/* Launch shape of the stage kernels: rows per tile of the y-march (2D) or
+ * planes per z-tile (3D).  lf_init picks it from the mesh size and the SM
+ * count unless lf_config.tile_rows sets it.  Results do not depend on it,
+ * bit for bit.  lf_set_tile_rows: 1 <= rows <= 4096, LF_ERR_ARG for 1D
+ * meshes; synchronises.  lf_get_tile_rows: the current value (0 in 1D). */
+lf_status lf_set_tile_rows(lf_ctx* ctx, int32_t rows);
+lf_status lf_get_tile_rows(lf_ctx* ctx, int32_t* rows);
+
+/* Times trial_steps CFL steps (after one warm-up step) for each candidate
+ * tile height (2D: 4, 8, 16, 32, 64, 128 rows; 3D: 8, 16, 32, 64 planes) on
+ * the current state, keeps the fastest and restores the state, t, dt and the
+ * step count (the trial steps leave no trace).  Allocates a temporary copy of
+ * the state.  chosen_rows (nullable) receives the pick.  Needs a state
+ * (LF_ERR_STATE) and a 2D or 3D mesh (LF_ERR_ARG).  Synchronises. */
+lf_status lf_autotune(lf_ctx* ctx, int32_t trial_steps, int32_t* chosen_rows);
 
 /* Stage tracing.  While enabled, every predictor (stage 0) and corrector
  * (stage 1) kernel launch is bracketed by CUDA events recorded on the

@@ -47,7 +47,7 @@ const char* validate(const lf_config* c) {
   const long long nz = c->dim == 3 ? c->nz : 1;
   if ((long long)c->nx * c->ny * nz > (1LL << 31)) return "mesh larger than 2^31 cells";
   if (c->dim == 3 && (!(c->zmax > c->zmin) || !std::isfinite(c->zmax - c->zmin))) return "need zmin < zmax";
-  if (c->reserved != 0) return "reserved must be 0";
+  if (c->tile_rows < 0 || c->tile_rows > 4096) return "tile_rows must be in 0 .. 4096";
   if (c->limiter < 0 || c->limiter > 2) return "unknown limiter";
   if (c->bc < 0 || c->bc > 1) return "unknown boundary condition";
   if (c->precision != LF_FP64 && c->precision != LF_FP32) return "unknown precision";
@@ -319,6 +319,15 @@ lf_status lf_init(const lf_config* cfg, void* stream, lf_ctx** out) {
     set_err(nullptr, "cannot select CUDA device %d", cfg->device);
     delete c;
     return LF_ERR_CUDA;
+  }
+  {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess) sms = 0;
+    const int cpl = c->elem == 4 ? 2 : 1;
+    if (cfg->dim == 2) m.ty = cfg->tile_rows > 0 ? cfg->tile_rows : lf::auto_tile_rows(m, cpl, sms);
+    if (cfg->dim == 3)
+      c->mesh3.tz = cfg->tile_rows > 0 ? cfg->tile_rows
+                                       : lf::auto_tile_planes(c->mesh3, cpl, lf::stage3d_rows_per_cta(), sms);
   }
   const size_t state_bytes = nf * (size_t)m.plane * c->elem;
   cudaError_t e = cudaSuccess;
@@ -807,6 +816,111 @@ lf_status lf_profile_read(lf_ctx* c, double ms[2], int64_t launches[2]) {
     ms[c->ev_stage[k]] += t;
     launches[c->ev_stage[k]] += 1;
   }
+  return LF_OK;
+}
+
+namespace {
+
+// Rows (2D) or planes (3D) per tile of the march; 0 for 1D meshes.
+int tile_of(const lf_ctx* c) { return c->cfg.dim == 3 ? c->mesh3.tz : c->cfg.dim == 2 ? c->mesh.ty : 0; }
+
+void set_tile(lf_ctx* c, int rows) {
+  if (c->cfg.dim == 3) c->mesh3.tz = rows;
+  else c->mesh.ty = rows;
+  if (c->run_graph) {  // the recorded steps carry the old launch shape
+    cudaGraphExecDestroy(c->run_graph);
+    c->run_graph = nullptr;
+  }
+}
+
+}  // namespace
+
+lf_status lf_set_tile_rows(lf_ctx* c, int32_t rows) {
+  if (!c) return LF_ERR_ARG;
+  if (c->cfg.dim == 1 || rows < 1 || rows > 4096) {
+    set_err(c, "lf_set_tile_rows: needs a 2D or 3D mesh and 1 <= rows <= 4096");
+    return LF_ERR_ARG;
+  }
+  DeviceGuard g(c->cfg.device);
+  LF_CUDA(c, cudaStreamSynchronize(c->stream));  // a replay in flight keeps the old graph
+  set_tile(c, rows);
+  return LF_OK;
+}
+
+lf_status lf_get_tile_rows(lf_ctx* c, int32_t* rows) {
+  if (!c || !rows) return LF_ERR_ARG;
+  *rows = tile_of(c);
+  return LF_OK;
+}
+
+lf_status lf_autotune(lf_ctx* c, int32_t trial_steps, int32_t* chosen_rows) {
+  if (!c) return LF_ERR_ARG;
+  if (c->cfg.dim == 1 || trial_steps < 1) {
+    set_err(c, "lf_autotune: needs a 2D or 3D mesh and trial_steps >= 1");
+    return LF_ERR_ARG;
+  }
+  if (!c->has_state) {
+    set_err(c, "lf_autotune: no state set");
+    return LF_ERR_STATE;
+  }
+  DeviceGuard g(c->cfg.device);
+  const size_t bytes = c->nf * (size_t)c->mesh.plane * c->elem;
+  void* save = nullptr;
+  lf::Scalars* save_sc = nullptr;
+  LF_CUDA(c, cudaMalloc(&save, bytes));
+  cudaError_t e = cudaMalloc(&save_sc, sizeof(lf::Scalars));
+  if (e != cudaSuccess) {
+    cudaFree(save);
+    return cuda_fail(c, e, "lf_autotune: cudaMalloc");
+  }
+  // the trial steps advance the state: copy it (and dt, t, the step count)
+  // and put it back after every candidate
+  e = cudaMemcpyAsync(save, c->U, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(save_sc, c->sc, sizeof(lf::Scalars), cudaMemcpyDeviceToDevice, c->stream);
+  const int cand2[] = {4, 8, 16, 32, 64, 128};
+  const int cand3[] = {8, 16, 32, 64};
+  const int* cand = c->cfg.dim == 3 ? cand3 : cand2;
+  const int ncand = c->cfg.dim == 3 ? 4 : 6;
+  const bool profiling = c->profiling;
+  c->profiling = false;
+  const int before = tile_of(c);
+  int best = before;
+  float best_ms = 1e30f;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  lf_status st = e == cudaSuccess ? LF_OK : cuda_fail(c, e, "lf_autotune");
+  for (int i = 0; i < ncand && st == LF_OK; ++i) {
+    set_tile(c, cand[i]);
+    if ((st = lf::enqueue_step(c, 0.0)) != LF_OK) break;  // warm-up
+    if ((e = cudaEventRecord(t0, c->stream)) != cudaSuccess) break;
+    for (int k = 0; k < trial_steps && st == LF_OK; ++k) st = lf::enqueue_step(c, 0.0);
+    if (st != LF_OK) break;
+    if ((e = cudaEventRecord(t1, c->stream)) != cudaSuccess) break;
+    if ((e = cudaEventSynchronize(t1)) != cudaSuccess) break;
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, t0, t1)) != cudaSuccess) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cand[i];
+    }
+    if ((e = cudaMemcpyAsync(c->U, save, bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(c->sc, save_sc, sizeof(lf::Scalars), cudaMemcpyDeviceToDevice, c->stream)) !=
+        cudaSuccess)
+      break;
+  }
+  if (st == LF_OK && e != cudaSuccess) st = cuda_fail(c, e, "lf_autotune");
+  cudaMemcpyAsync(c->U, save, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(c->sc, save_sc, sizeof(lf::Scalars), cudaMemcpyDeviceToDevice, c->stream);
+  cudaStreamSynchronize(c->stream);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  cudaFree(save);
+  cudaFree(save_sc);
+  c->profiling = profiling;
+  set_tile(c, st == LF_OK ? best : before);
+  if (st != LF_OK) return st;
+  if (chosen_rows) *chosen_rows = best;
   return LF_OK;
 }
 

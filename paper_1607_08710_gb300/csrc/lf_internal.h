@@ -39,7 +39,26 @@ struct MeshDesc {
   int vec;           // 1: pitch and plane even and every state buffer 16-byte
                      // aligned, so two adjacent cells may be moved as one vector
   int nspecies = 0;  // transported mass fractions: planes 4 .. 3 + nspecies hold rho y_k
+  int ty = 0;        // rows per tile of the 2D stage kernels (0: the compiled default)
 };
+
+// Rows per tile for a 2D mesh.  A tile pays for its two halo rows below and
+// above and for filling its copy pipeline, so tiles are 64 rows unless the
+// grid of (strips x tiles) one-warp CTAs is too small for the GPU: halved
+// down to 16 rows while there are fewer than 32 CTAs per SM (about two
+// resident waves), then down to 4 rows while fewer than 8.  (Fitted to
+// GB300 timings of square meshes from 256^2 to 8192^2; lf_autotune times the
+// candidates on the actual mesh instead.)  cpl: cells per lane (2 for FP32,
+// 1 for FP64); sms <= 0: keep 64.
+inline int auto_tile_rows(const MeshDesc& m, int cpl, int sms) {
+  const int out_cols = 32 * cpl - 4;
+  const long long strips = (m.nx + out_cols - 1) / out_cols;
+  auto ctas = [&](int ty) { return strips * ((m.ny + ty - 1) / ty); };
+  int ty = 64;
+  while (ty > 16 && ctas(ty) < 32LL * sms) ty /= 2;
+  while (ty > 4 && ctas(ty) < 8LL * sms) ty /= 2;
+  return ty;
+}
 
 // Largest nspecies the stage kernels are built for.
 constexpr int MAX_SPECIES = 2;

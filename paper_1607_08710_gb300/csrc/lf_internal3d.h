@@ -18,7 +18,20 @@ struct Mesh3Desc {
   int bc, limiter, riemann, nspecies;
   double gamma, beta;
   double rdx, rdy, rdz;
+  int tz = 0;         // planes per z-tile of the 3D stage kernels (0: the compiled default)
 };
+
+// Planes per z-tile for a 3D mesh: 64, halved down to 8 while the grid of
+// (strips x row blocks x z-tiles) CTAs of rows_per_cta warps gives fewer
+// than 6 CTAs per SM (two waves of the three resident CTAs).  cpl: cells per
+// lane; sms <= 0: keep 64.
+inline int auto_tile_planes(const Mesh3Desc& m, int cpl, int rows_per_cta, int sms) {
+  const int out_cols = 32 * cpl - 4;
+  const long long cols = (long long)((m.nx + out_cols - 1) / out_cols) * ((m.ny + rows_per_cta - 1) / rows_per_cta);
+  int tz = 64;
+  while (tz > 8 && cols * ((m.nz + tz - 1) / tz) < 6LL * sms) tz /= 2;
+  return tz;
+}
 
 // The 2D descriptor whose fields the shared device helpers read (Phys: gamma,
 // beta, riemann, 1/dx, 1/dy), and the row view of the mesh used by the
@@ -61,5 +74,7 @@ cudaError_t launch_species_to_cons3d(const Mesh3Desc& m, const float* y, float* 
 cudaError_t launch_species_to_cons3d(const Mesh3Desc& m, const double* y, double* U, cudaStream_t s);
 cudaError_t launch_cons_to_species3d(const Mesh3Desc& m, const float* U, float* y, cudaStream_t s);
 cudaError_t launch_cons_to_species3d(const Mesh3Desc& m, const double* U, double* y, cudaStream_t s);
+// Warps (= rows) per CTA of the 3D stage kernels.
+int stage3d_rows_per_cta();
 
 }  // namespace lf

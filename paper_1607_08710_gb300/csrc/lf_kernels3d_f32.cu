@@ -4,6 +4,8 @@
 
 namespace lf {
 
+int stage3d_rows_per_cta() { return ROWS3; }
+
 cudaError_t launch_stage3d(int stage, const Mesh3Desc& m, const float* Uin, const float* Un, float* out, Scalars* sc,
                            cudaStream_t s) {
   return launch_stage3d_impl<float>(stage, m, Uin, Un, out, sc, s);

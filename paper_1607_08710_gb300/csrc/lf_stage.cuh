@@ -550,8 +550,9 @@ stage2d_kernel(const MeshDesc m, const T* __restrict__ Uin, const T* Un, T* out,
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i0 = (blockIdx.x * STAGE_WARPS + warp) * StripGeom<CPL>::OUT;
   if (i0 >= m.nx) return;  // whole warp
-  const int j0 = blockIdx.y * TY;
-  const int jend = min(j0 + TY, m.ny);
+  const int ty = m.ty > 0 ? m.ty : TY;
+  const int j0 = blockIdx.y * ty;
+  const int jend = min(j0 + ty, m.ny);
   const double hs = StageCoef<STAGE>::beta;
   const T cx = T(hs * dtd * m.rdx), cy = T(hs * dtd * m.rdy);
   T* ring = reinterpret_cast<T*>(lf_stage_smem + warp * Ring<T, CPL, NF>::warp_bytes(STAGE));
@@ -630,7 +631,8 @@ cudaError_t launch_stage_lim(int stage, const MeshDesc& m, const T* Uin, const T
       default: stage1d_kernel<T, LIM, 3, CPL, NF><<<grid, block, 0, s>>>(m, Uin, Un, out, sc);
     }
   } else {
-    dim3 grid((strips + STAGE_WARPS - 1) / STAGE_WARPS, (m.ny + TY - 1) / TY);
+    const int ty = m.ty > 0 ? m.ty : TY;
+    dim3 grid((strips + STAGE_WARPS - 1) / STAGE_WARPS, (m.ny + ty - 1) / ty);
     const size_t smem = STAGE_WARPS * Ring<T, CPL, NF>::warp_bytes(stage);
     switch (stage) {
       case 0: stage2d_kernel<T, LIM, 0, CPL, TY, NF><<<grid, block, smem, s>>>(m, Uin, Un, out, sc); break;

@@ -335,7 +335,7 @@ __device__ __forceinline__ void march_plane3(const Phys<V>& P, const Mesh3Desc& 
 template <typename T, int NF> struct MinBlocks3 { static constexpr int value = NF == 5 ? LF_3D_MIN_BLOCKS : 2; };
 template <int NF> struct MinBlocks3<double, NF> { static constexpr int value = 1; };
 
-// Grid: (strips, ceil(ny / ROWS3), ceil(nz / TZ3)); ROWS3 warps per CTA.
+// Grid: (strips, ceil(ny / ROWS3), ceil(nz / tz)), tz = m.tz or TZ3; ROWS3 warps per CTA.
 template <typename T, int LIM, int STAGE, int NF>
 __global__ void __launch_bounds__(ROWS3 * 32, (MinBlocks3<T, NF>::value))
 stage3d_kernel(const Mesh3Desc m, const T* __restrict__ Uin, const T* Un, T* out, Scalars* sc) {
@@ -359,8 +359,9 @@ stage3d_kernel(const Mesh3Desc m, const T* __restrict__ Uin, const T* Un, T* out
   A.P = A.ring + RING3 * SM::PLANE_IN;
   A.unr = A.P + SM::PLANE_IN;
   A.j0 = j0;
-  A.k0 = blockIdx.z * TZ3;
-  A.kend = min(A.k0 + TZ3, m.nz);
+  const int tz = m.tz > 0 ? m.tz : TZ3;
+  A.k0 = blockIdx.z * tz;
+  A.kend = min(A.k0 + tz, m.nz);
   A.own_off = (long long)map_row(jrow, m.ny, m.bc) * m.pitch;
   A.halo_rr = warp < HALO3 ? (warp < 2 ? warp : ROWS3 + warp) : -1;
   A.halo_off = A.halo_rr >= 0 ? (long long)map_row(j0 - 2 + A.halo_rr, m.ny, m.bc) * m.pitch : 0;
@@ -435,7 +436,8 @@ cudaError_t launch_stage3d_lim(int stage, const Mesh3Desc& m, const T* Uin, cons
   constexpr int CPL = StageShape<T>::CPL;
   using SM = Smem3<T, CPL, NF>;
   const int strips = (m.nx + StripGeom<CPL>::OUT - 1) / StripGeom<CPL>::OUT;
-  const dim3 grid(strips, (m.ny + ROWS3 - 1) / ROWS3, (m.nz + TZ3 - 1) / TZ3);
+  const int tz = m.tz > 0 ? m.tz : TZ3;
+  const dim3 grid(strips, (m.ny + ROWS3 - 1) / ROWS3, (m.nz + tz - 1) / tz);
   const dim3 block(ROWS3 * 32);
   const size_t smem = SM::bytes(stage);
   cudaError_t e = cudaSuccess;

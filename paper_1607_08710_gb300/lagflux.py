@@ -45,7 +45,7 @@ class lf_config(ctypes.Structure):
         ("cfl", ctypes.c_double),
         ("beta", ctypes.c_double),
         ("nz", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("tile_rows", ctypes.c_int32),
         ("zmin", ctypes.c_double),
         ("zmax", ctypes.c_double),
     ]
@@ -76,6 +76,9 @@ SIGNATURES = {
     "lf_get_time": (ctypes.c_int, [_vp, _P(_d), _P(_i64)]),
     "lf_conservation_sums": (ctypes.c_int, [_vp, _P(_d)]),
     "lf_sync": (ctypes.c_int, [_vp]),
+    "lf_set_tile_rows": (ctypes.c_int, [_vp, _i32]),
+    "lf_get_tile_rows": (ctypes.c_int, [_vp, _P(_i32)]),
+    "lf_autotune": (ctypes.c_int, [_vp, _i32, _P(_i32)]),
     "lf_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lf_profile_read": (ctypes.c_int, [_vp, _P(_d), _P(_i64)]),
     "lf_step_noalloc": (ctypes.c_int, [_P(lf_config), _vp, _vp, _d, _P(_d), _vp]),
@@ -138,12 +141,13 @@ class Config:
     nz: int = 1
     zmin: float = 0.0
     zmax: float = 1.0
+    tile_rows: int = 0  # rows per tile of the 2D stage kernels; 0: chosen from the mesh and the GPU
 
     def to_c(self) -> lf_config:
         return lf_config(self.dim, self.nx, self.ny if self.dim >= 2 else 1, LIMITERS[self.limiter], BCS[self.bc],
                          PRECISIONS[self.precision], RIEMANN[self.riemann], self.device, self.time_order,
                          self.nspecies, self.xmin, self.xmax, self.ymin, self.ymax, self.gamma, self.cfl, self.beta,
-                         self.nz if self.dim == 3 else 1, 0, self.zmin, self.zmax)
+                         self.nz if self.dim == 3 else 1, self.tile_rows, self.zmin, self.zmax)
 
     @property
     def nfields(self) -> int:
@@ -364,6 +368,25 @@ class LagrangeFlux:
 
     def sync(self):
         self._check(_lib.lf_sync(self._h))
+
+    # -- launch shape ------------------------------------------------------
+    @property
+    def tile_rows(self) -> int:
+        """Rows per tile of the y-march (2D) or planes per z-tile (3D); 0 in 1D."""
+        r = ctypes.c_int32()
+        self._check(_lib.lf_get_tile_rows(self._h, ctypes.byref(r)))
+        return r.value
+
+    @tile_rows.setter
+    def tile_rows(self, rows: int):
+        self._check(_lib.lf_set_tile_rows(self._h, int(rows)))
+
+    def autotune(self, trial_steps: int = 3) -> int:
+        """Times the candidate tile heights on the current state (which is left
+        unchanged), keeps the fastest and returns it."""
+        r = ctypes.c_int32()
+        self._check(_lib.lf_autotune(self._h, int(trial_steps), ctypes.byref(r)))
+        return r.value
 
     # -- discrete adjoint ------------------------------------------------
     def adjoint_forward(self, nsteps: int) -> np.ndarray:

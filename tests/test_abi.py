@@ -63,7 +63,7 @@ def test_status_strings(lib):
 
 @pytest.mark.parametrize(
     "field,value",
-    [("dim", 4), ("dim", 0), ("nz", 2), ("reserved", 1), ("nx", 0), ("ny", 0), ("limiter", 7), ("bc", 2), ("precision", 5), ("riemann", 2), ("gamma", 1.0),
+    [("dim", 4), ("dim", 0), ("nz", 2), ("tile_rows", -1), ("tile_rows", 4097), ("nx", 0), ("ny", 0), ("limiter", 7), ("bc", 2), ("precision", 5), ("riemann", 2), ("gamma", 1.0),
      ("gamma", 3.5), ("cfl", 0.0), ("cfl", 1.5), ("beta", 2.5), ("xmax", 0.0), ("device", -1), ("nspecies", 3),
      ("nspecies", -1), ("time_order", 4)],
 )

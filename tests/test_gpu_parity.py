@@ -7,7 +7,8 @@ Bars:
     input after tens of steps (single-precision rounding, ~6e-8 per
     operation, grown through the run; the bound for the smooth-flow precision
     study is 1e-5, checked in test_gpu_precision.py).
-Sizes span several 28-column warp strips and 64-row tiles with ragged tails.
+Sizes span several warp strips (60 output columns in FP32, 28 in FP64) and 64-row tiles with
+ragged tails.
 """
 import math
 
