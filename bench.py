@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--steps3d", type=int, default=50)
     ap.add_argument("--batch-problems", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=300)
+    ap.add_argument("--tile-rows", type=int, default=0,
+                    help="rows per tile of the 2D stage kernels on the main mesh (0: chosen by lf_init)")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adjoint-size", type=int, default=512)
     ap.add_argument("--adjoint-steps", type=int, default=256)
@@ -391,9 +393,11 @@ def run_ours(args, dist):
     prec = args.precision
     tdt = torch.float32 if prec == "fp32" else torch.float64
     prim = inputs.kelvin_helmholtz(n, n, seed=0).stack()
-    kw = dict(nx=n, ny=n, limiter="vanleer", bc="periodic", cfl=0.45, device=dist.local_rank)
+    kw = dict(nx=n, ny=n, limiter="vanleer", bc="periodic", cfl=0.45, device=dist.local_rank,
+              tile_rows=args.tile_rows)
 
     solver = LagrangeFlux(Config(precision=prec, **kw))
+    tile_used = solver.tile_rows
     q = torch.from_numpy(prim).to(dev, tdt)
     solver.set_primitive(q[0], q[1], q[2], q[3])
     del q
@@ -646,7 +650,8 @@ def run_ours(args, dist):
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
-        "config": dict(workload_config(args), parallelism=f"replicas x{dist.world}" if dist.world > 1 else "single GPU"),
+        "config": dict(workload_config(args), tile_rows=tile_used,
+                       parallelism=f"replicas x{dist.world}" if dist.world > 1 else "single GPU"),
         "roofline": roofline, "kernels": kernels, "gpu_launches": 4 * args.steps, "clocks": clk,
     }
     line.update(out)

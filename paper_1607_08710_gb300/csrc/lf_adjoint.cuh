@@ -116,9 +116,18 @@ __device__ __forceinline__ void load_prim(const Phys<T>& P, const T* U, long lon
   q[3] = P.gm1 * (Uc[3] - T(0.5) * (Uc[1] * u + Uc[2] * v));
 }
 
-// Face kernel.  DIR 0: x-faces, nf = nx + 1 per row, ny rows; DIR 1: y-faces,
-// nf = ny + 1 per column, nx columns.  Output Fq[(f_line * nf + f) * 8 + ...]:
-// cotangents of (qL[0..3], qR[0..3]).
+// Slot of face f (0 .. n) of line `line` in the face-cotangent arrays: x-faces
+// row by row ([row][face]), y-faces face row by face row ([face][column]), so
+// that neighbouring threads, which take neighbouring x positions, touch
+// neighbouring slots and neighbouring cells in both directions.
+template <int DIR>
+__device__ __forceinline__ long long face_slot(const MeshDesc& m, int line, int f) {
+  return DIR == 0 ? (long long)line * (m.nx + 1) + f : (long long)f * m.nx + line;
+}
+
+// Face kernel.  DIR 0: x-faces, nx + 1 per row, ny rows; DIR 1: y-faces,
+// ny + 1 per column, nx columns.  Output Fq[face_slot * 8 + ...]: cotangents
+// of (qL[0..3], qR[0..3]).
 template <typename T, int LIM, int DIR>
 __global__ void face_vjp_kernel(const MeshDesc m, const T* __restrict__ U, const T* __restrict__ mu, T* Fq) {
   const Phys<T> P(m);
@@ -128,7 +137,9 @@ __global__ void face_vjp_kernel(const MeshDesc m, const T* __restrict__ U, const
   const T h = DIR == 0 ? T(m.rdx) : T(m.rdy);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    const int line = (int)(t / (n + 1)), f = (int)(t - (long long)line * (n + 1));
+    // consecutive threads: consecutive faces of a row (x) or columns (y)
+    const int line = DIR == 0 ? (int)(t / (n + 1)) : (int)(t % lines);
+    const int f = DIR == 0 ? (int)(t - (long long)line * (n + 1)) : (int)(t / lines);
     auto cell_idx = [&](int c) -> long long {
       const int cm = map_index(c, n, m.bc);
       return DIR == 0 ? (long long)line * m.pitch + cm : (long long)cm * m.pitch + line;
@@ -155,7 +166,7 @@ __global__ void face_vjp_kernel(const MeshDesc m, const T* __restrict__ U, const
     }
     T qLb[4] = {T(0), T(0), T(0), T(0)}, qRb[4] = {T(0), T(0), T(0), T(0)};
     lagrange_flux_vjp<T, DIR>(P, qL, qR, nu, qLb, qRb);
-    T* o = Fq + t * 8;
+    T* o = Fq + face_slot<DIR>(m, line, f) * 8;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       o[k] = qLb[k];
@@ -178,7 +189,7 @@ __device__ __forceinline__ void gather_dir(const Phys<T>& P, const MeshDesc& m, 
   };
   auto face = [&](int f, int part, int k) -> T {  // part 0: qL cotangent, 1: qR cotangent
     if (f < 0 || f > n) return T(0);
-    return Fq[((long long)line * (n + 1) + f) * 8 + part * 4 + k];
+    return Fq[face_slot<DIR>(m, line, f) * 8 + part * 4 + k];
   };
   // every image v of this cell in [-2, n+1] (itself, ghost copies, periodic images)
   int cand[9] = {pos, -2, -1, n, n + 1, pos - n, pos + n, pos - 2 * n, pos + 2 * n};
