@@ -64,6 +64,17 @@ __device__ __forceinline__ bool inner_strip(const MeshDesc& m, int i0) {
 }
 
 // Rows are uniform across a warp; wrap or clamp without an integer division.
+// map_row_ahead: for rows known to be >= 0 (the rows a march prefetches
+// ahead of itself); stating that saves the march a wrap loop per row, which
+// measured 5% of the 2D stage's time once the tile height became a runtime
+// value and the compiler could no longer infer it.
+__device__ __forceinline__ int map_row_ahead(int r, int n, int bc) {
+  if (bc == BC_PERIODIC) {
+    while (r >= n) r -= n;
+    return r;
+  }
+  return r >= n ? n - 1 : r;
+}
 __device__ __forceinline__ int map_row(int r, int n, int bc) {
   if (bc == BC_PERIODIC) {
     while (r < 0) r += n;
@@ -366,7 +377,7 @@ __device__ __forceinline__ void march_row(const Phys<V>& P, const MeshDesc& m,
   // (rows r-1) are no longer read, so the branch-free row body costs two idle
   // copies per tile.  strip_tile_impl drains them before returning.
   issue_row<T, CPL, NF, MODE>(A.ring_in + ring_in_plus(si, AHEAD_IN) * ROW, A.P, L,
-                              map_row(r + AHEAD_IN, m.ny, m.bc) * m.pitch, lane);
+                              map_row_ahead(r + AHEAD_IN, m.ny, m.bc) * m.pitch, lane);
   if (STAGE >= 1)  // U^n row r+2 lives in register slot S2's ring buffer
     issue_out_cells<T, CPL, NF, MODE>(A.ring_un + S2 * ROW, A.N, L, min(r + AHEAD_UN, m.ny - 1) * m.pitch, lane);
   cp_commit();

@@ -131,11 +131,13 @@ struct Args3 {
 
 // This warp's copies of input plane `k` into its ring slot: its own row and,
 // for warps 0-3, one halo row, all fields, each lane copying its own CPL cells.
-template <typename T, int STAGE, int CPL, int NF>
+// AHEAD: k >= 0 (the march's prefetch; the prologue also asks for k0-2, k0-1).
+template <typename T, int STAGE, int CPL, int NF, bool AHEAD = false>
 __device__ __forceinline__ void issue_plane3(const Mesh3Desc& m, const Args3<T, STAGE, NF>& A, const LaneCols<CPL>& L,
                                              int k, int warp, int lane) {
   using SM = Smem3<T, CPL, NF>;
-  const long long zoff = (long long)map_row(k, m.nz, m.bc) * m.ny * m.pitch;
+  const int kz = AHEAD ? map_row_ahead(k, m.nz, m.bc) : map_row(k, m.nz, m.bc);
+  const long long zoff = (long long)kz * m.ny * m.pitch;
   T* slot = A.ring + ((k - A.k0 + 4) & 3) * SM::PLANE_IN + CPL * lane;
   const T* src = A.Uin + zoff + A.own_off;
   const T* hsrc = A.Uin + zoff + A.halo_off;
@@ -221,7 +223,7 @@ __device__ __forceinline__ void march_plane3(const Phys<V>& P, const Mesh3Desc& 
     write_seg<T, CPL, NF>(A.P + rr * SM::ROWSEG, lane, qh);
   }
   // next copies: input plane k+3 (into plane k-1's slot), U^n plane k+1
-  issue_plane3<T, STAGE, CPL, NF>(m, A, L, k + 3, warp, lane);
+  issue_plane3<T, STAGE, CPL, NF, true>(m, A, L, k + 3, warp, lane);
   issue_un3<T, STAGE, CPL, NF>(m, A, L, k + 1, warp, lane, jrow);
   cp_commit();
   __syncthreads();
