@@ -6,7 +6,8 @@
 // sequence is frozen for the derivative).  lf_adjoint_backward sweeps the
 // segments backwards: it recomputes a segment's states from its checkpoint,
 // then reverses its steps one by one with the face/cell adjoint kernels.
-// Memory: ceil(N/S) + S states plus a few work states, instead of N.
+// Memory: ceil(N/S) + S states plus a few work states, instead of N, and in
+// FP64 the prep tables of one state (28 values per cell).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -50,6 +51,10 @@ lf_status backward_t(lf_ctx* c) {
   T* lamstar = static_cast<T*>(A.lamstar);
   T* fx = static_cast<T*>(A.fx);
   T* fy = static_cast<T*>(A.fy);
+  constexpr bool kTables = sizeof(T) == 8;
+  T* Q = static_cast<T*>(A.prep);  // FP64 only
+  T* tabx = kTables ? Q + 4 * (size_t)m.nx * m.ny : nullptr;
+  T* taby = kTables ? tabx + 12 * (size_t)(m.nx + 2) * m.ny : nullptr;
   T* Us = static_cast<T*>(c->Ustar);
   LF_CUDA(c, lf::launch_reset_scalars(A.sc, c->cfg.cfl, s));
   const int nseg = (A.nsteps + A.seg - 1) / A.seg;
@@ -73,14 +78,27 @@ lf_status backward_t(lf_ctx* c) {
       LF_CUDA(c, lf::launch_begin_step(A.sc, dt, s));
       LF_CUDA(c, lf::launch_stage<T>(0, m, Un, Un, Us, A.sc, s));
       LF_CUDA(c, lf::launch_end_step(A.sc, s));
-      // lambda* = lambda/2 - dt/2 (dD/dU)(U*)^T lambda
-      LF_CUDA(c, lf::launch_face_vjp<T>(m, 0, Us, lam, fx, s));
-      LF_CUDA(c, lf::launch_face_vjp<T>(m, 1, Us, lam, fy, s));
-      LF_CUDA(c, lf::launch_cell_vjp<T>(m, Us, fx, fy, lam, 0.5, nullptr, 0.0, -0.5 * dt, lamstar, s));
-      // lambda <- lambda/2 + lambda* - dt (dD/dU)(U^n)^T lambda*
-      LF_CUDA(c, lf::launch_face_vjp<T>(m, 0, Un, lamstar, fx, s));
-      LF_CUDA(c, lf::launch_face_vjp<T>(m, 1, Un, lamstar, fy, s));
-      LF_CUDA(c, lf::launch_cell_vjp<T>(m, Un, fx, fy, lam, 0.5, lamstar, 1.0, -dt, lam, s));
+      // lambda* = lambda/2 - dt/2 (dD/dU)(U*)^T lambda, then
+      // lambda <- lambda/2 + lambda* - dt (dD/dU)(U^n)^T lambda*.  FP64 reads
+      // the forward quantities from prep tables (its divisions dominate);
+      // FP32 recomputes them in the two passes (measured faster there).
+      if (kTables) {
+        LF_CUDA(c, lf::launch_adjoint_prep<T>(m, Us, Q, tabx, taby, s));
+        LF_CUDA(c, lf::launch_face_vjp<T>(m, 0, Q, tabx, lam, fx, s));
+        LF_CUDA(c, lf::launch_face_vjp<T>(m, 1, Q, taby, lam, fy, s));
+        LF_CUDA(c, lf::launch_cell_vjp<T>(m, Q, fx, fy, tabx, taby, lam, 0.5, nullptr, 0.0, -0.5 * dt, lamstar, s));
+        LF_CUDA(c, lf::launch_adjoint_prep<T>(m, Un, Q, tabx, taby, s));
+        LF_CUDA(c, lf::launch_face_vjp<T>(m, 0, Q, tabx, lamstar, fx, s));
+        LF_CUDA(c, lf::launch_face_vjp<T>(m, 1, Q, taby, lamstar, fy, s));
+        LF_CUDA(c, lf::launch_cell_vjp<T>(m, Q, fx, fy, tabx, taby, lam, 0.5, lamstar, 1.0, -dt, lam, s));
+      } else {
+        LF_CUDA(c, lf::launch_face_vjp_direct<T>(m, 0, Us, lam, fx, s));
+        LF_CUDA(c, lf::launch_face_vjp_direct<T>(m, 1, Us, lam, fy, s));
+        LF_CUDA(c, lf::launch_cell_vjp_direct<T>(m, Us, fx, fy, lam, 0.5, nullptr, 0.0, -0.5 * dt, lamstar, s));
+        LF_CUDA(c, lf::launch_face_vjp_direct<T>(m, 0, Un, lamstar, fx, s));
+        LF_CUDA(c, lf::launch_face_vjp_direct<T>(m, 1, Un, lamstar, fy, s));
+        LF_CUDA(c, lf::launch_cell_vjp_direct<T>(m, Un, fx, fy, lam, 0.5, lamstar, 1.0, -dt, lam, s));
+      }
     }
   }
   return LF_OK;
@@ -96,6 +114,7 @@ void lf::free_adjoint(lf_ctx* c) {
   cudaFree(A.lamstar);
   cudaFree(A.fx);
   cudaFree(A.fy);
+  cudaFree(A.prep);
   cudaFree(A.dts_dev);
   cudaFree(A.sc);
   A = lf_ctx::Adjoint();
@@ -137,6 +156,11 @@ lf_status lf_adjoint_forward(lf_ctx* c, int32_t nsteps, double* dts_out) {
   if (lf_status st = grow(c, &A.fx, &fx_cap, faces * 8 * c->elem)) return st;
   if (lf_status st = grow(c, &A.fy, &fy_cap, faces * 8 * c->elem)) return st;
   A.face_cap = fx_cap < fy_cap ? fx_cap : fy_cap;
+  if (c->elem == 8) {  // FP64 reverse sweeps read prep tables
+    const size_t prep_elems =
+        4 * (size_t)m.nx * m.ny + 12 * ((size_t)(m.nx + 2) * m.ny + (size_t)(m.ny + 2) * m.nx);
+    if (lf_status st = grow(c, &A.prep, &A.prep_cap, prep_elems * c->elem)) return st;
+  }
   if (lf_status st = grow(c, reinterpret_cast<void**>(&A.dts_dev), &A.dts_cap, nsteps * sizeof(double))) return st;
   if (lf_status st = grow(c, reinterpret_cast<void**>(&A.sc), &sc_cap, sizeof(lf::Scalars))) return st;
   for (int n = 0; n < nsteps; ++n) {

@@ -43,13 +43,14 @@ struct lf_ctx {
     int seg = 0;               // checkpoint interval
     std::vector<double> dts;   // frozen dt sequence
     size_t state_elems = 0;    // elements of one state (4 planes)
-    size_t ck_cap = 0, seg_cap = 0, face_cap = 0, dts_cap = 0;
+    size_t ck_cap = 0, seg_cap = 0, face_cap = 0, dts_cap = 0, prep_cap = 0;
     void* ck = nullptr;        // checkpoints: ceil(nsteps / seg) states
     void* segbuf = nullptr;    // recomputed states of one segment
     void* lam = nullptr;       // cotangent of the state
     void* lamstar = nullptr;   // cotangent of the predictor state
     void* fx = nullptr;        // face-state cotangents, x-faces
     void* fy = nullptr;        // face-state cotangents, y-faces
+    void* prep = nullptr;      // primitives (4 dense planes) and the x and y slope tables of one state
     double* dts_dev = nullptr; // dt of each forward step, recorded on the device
     lf::Scalars* sc = nullptr; // scalars of the recomputation
   } adj;

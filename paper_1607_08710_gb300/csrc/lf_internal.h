@@ -136,14 +136,26 @@ int batch_blocks_per_sm(int stage, int limiter);
 cudaError_t launch_batch_begin(Scalars* sc, int nprob, double dt_fixed, int* counters, cudaStream_t s);
 cudaError_t launch_batch_end(Scalars* sc, int nprob, cudaStream_t s);
 
-// Discrete adjoint (lf_adjoint.cuh).  Face pass: cotangents of the face
-// states of every x-face (dir 0) or y-face (dir 1) for the cell cotangent mu.
+// Discrete adjoint (lf_adjoint.cuh).  Prep: primitives Q (4 dense planes) of
+// the state U and the slope tables of x (tabx: (nx+2)*ny slots) and y (taby:
+// (ny+2)*nx slots), 12 values per slot.
 template <typename T>
-cudaError_t launch_face_vjp(const MeshDesc& m, int dir, const T* U, const T* mu, T* Fq, cudaStream_t s);
+cudaError_t launch_adjoint_prep(const MeshDesc& m, const T* U, T* Q, T* tabx, T* taby, cudaStream_t s);
+// Face pass: cotangents of the face states of every x-face (dir 0) or y-face
+// (dir 1) for the cell cotangent mu.
+template <typename T>
+cudaError_t launch_face_vjp(const MeshDesc& m, int dir, const T* Q, const T* tab, const T* mu, T* Fq,
+                            cudaStream_t s);
 // Cell pass: out = alpha X + beta Y + c (dD/dU)^T mu (X, Y nullable).
 template <typename T>
-cudaError_t launch_cell_vjp(const MeshDesc& m, const T* U, const T* Fx, const T* Fy, const T* X, double alpha,
-                            const T* Y, double beta, double c, T* out, cudaStream_t s);
+cudaError_t launch_cell_vjp(const MeshDesc& m, const T* Q, const T* Fx, const T* Fy, const T* tabx, const T* taby,
+                            const T* X, double alpha, const T* Y, double beta, double c, T* out, cudaStream_t s);
+// The same two passes recomputing the primitives and slopes from U (FP32).
+template <typename T>
+cudaError_t launch_face_vjp_direct(const MeshDesc& m, int dir, const T* U, const T* mu, T* Fq, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cell_vjp_direct(const MeshDesc& m, const T* U, const T* Fx, const T* Fy, const T* X, double alpha,
+                                   const T* Y, double beta, double c, T* out, cudaStream_t s);
 // Gradient with respect to the primitive initial fields (dense planes).
 template <typename T>
 cudaError_t launch_grad_prim(const MeshDesc& m, const T* U0, const T* lam, T* gq, cudaStream_t s);

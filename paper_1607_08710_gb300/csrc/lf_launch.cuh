@@ -80,36 +80,72 @@ cudaError_t launch_sums(const MeshDesc& m, const T* U, double* partials, int nbl
 }
 
 template <typename T, int LIM>
-cudaError_t launch_face_vjp_lim(const MeshDesc& m, int dir, const T* U, const T* mu, T* Fq, cudaStream_t s) {
-  const long long nfaces = dir == 0 ? (long long)(m.nx + 1) * m.ny : (long long)(m.ny + 1) * m.nx;
-  const int nb = aux_blocks(nfaces);
-  if (dir == 0) face_vjp_kernel<T, LIM, 0><<<nb, AUX_THREADS, 0, s>>>(m, U, mu, Fq);
-  else face_vjp_kernel<T, LIM, 1><<<nb, AUX_THREADS, 0, s>>>(m, U, mu, Fq);
+cudaError_t launch_slope_tables_lim(const MeshDesc& m, const T* Q, T* tabx, T* taby, cudaStream_t s) {
+  slope_table_kernel<T, LIM, 0><<<aux_blocks((long long)(m.nx + 2) * m.ny), AUX_THREADS, 0, s>>>(m, Q, tabx);
+  slope_table_kernel<T, LIM, 1><<<aux_blocks((long long)(m.ny + 2) * m.nx), AUX_THREADS, 0, s>>>(m, Q, taby);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_face_vjp(const MeshDesc& m, int dir, const T* U, const T* mu, T* Fq, cudaStream_t s) {
+cudaError_t launch_adjoint_prep(const MeshDesc& m, const T* U, T* Q, T* tabx, T* taby, cudaStream_t s) {
+  prim_planes_kernel<T><<<aux_blocks((long long)m.nx * m.ny), AUX_THREADS, 0, s>>>(m, U, Q);
   switch (m.limiter) {
-    case LIM_MINMOD: return launch_face_vjp_lim<T, LIM_MINMOD>(m, dir, U, mu, Fq, s);
-    case LIM_SWEBY: return launch_face_vjp_lim<T, LIM_SWEBY>(m, dir, U, mu, Fq, s);
-    default: return launch_face_vjp_lim<T, LIM_VANLEER>(m, dir, U, mu, Fq, s);
+    case LIM_MINMOD: return launch_slope_tables_lim<T, LIM_MINMOD>(m, Q, tabx, taby, s);
+    case LIM_SWEBY: return launch_slope_tables_lim<T, LIM_SWEBY>(m, Q, tabx, taby, s);
+    default: return launch_slope_tables_lim<T, LIM_VANLEER>(m, Q, tabx, taby, s);
   }
 }
 
 template <typename T>
-cudaError_t launch_cell_vjp(const MeshDesc& m, const T* U, const T* Fx, const T* Fy, const T* X, double alpha,
-                            const T* Y, double beta, double c, T* out, cudaStream_t s) {
+cudaError_t launch_face_vjp(const MeshDesc& m, int dir, const T* Q, const T* tab, const T* mu, T* Fq,
+                            cudaStream_t s) {
+  const long long nfaces = dir == 0 ? (long long)(m.nx + 1) * m.ny : (long long)(m.ny + 1) * m.nx;
+  const int nb = aux_blocks(nfaces);
+  if (dir == 0) face_vjp_kernel<T, 0><<<nb, AUX_THREADS, 0, s>>>(m, Q, tab, mu, Fq);
+  else face_vjp_kernel<T, 1><<<nb, AUX_THREADS, 0, s>>>(m, Q, tab, mu, Fq);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cell_vjp(const MeshDesc& m, const T* Q, const T* Fx, const T* Fy, const T* tabx, const T* taby,
+                            const T* X, double alpha, const T* Y, double beta, double c, T* out, cudaStream_t s) {
+  cell_vjp_kernel<T><<<aux_blocks((long long)m.nx * m.ny), AUX_THREADS, 0, s>>>(m, Q, Fx, Fy, tabx, taby, X, T(alpha),
+                                                                               Y, T(beta), T(c), out);
+  return cudaGetLastError();
+}
+
+template <typename T, int LIM>
+cudaError_t launch_face_vjp_direct_lim(const MeshDesc& m, int dir, const T* U, const T* mu, T* Fq, cudaStream_t s) {
+  const long long nfaces = dir == 0 ? (long long)(m.nx + 1) * m.ny : (long long)(m.ny + 1) * m.nx;
+  const int nb = aux_blocks(nfaces);
+  if (dir == 0) face_vjp_direct_kernel<T, LIM, 0><<<nb, AUX_THREADS, 0, s>>>(m, U, mu, Fq);
+  else face_vjp_direct_kernel<T, LIM, 1><<<nb, AUX_THREADS, 0, s>>>(m, U, mu, Fq);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_face_vjp_direct(const MeshDesc& m, int dir, const T* U, const T* mu, T* Fq, cudaStream_t s) {
+  switch (m.limiter) {
+    case LIM_MINMOD: return launch_face_vjp_direct_lim<T, LIM_MINMOD>(m, dir, U, mu, Fq, s);
+    case LIM_SWEBY: return launch_face_vjp_direct_lim<T, LIM_SWEBY>(m, dir, U, mu, Fq, s);
+    default: return launch_face_vjp_direct_lim<T, LIM_VANLEER>(m, dir, U, mu, Fq, s);
+  }
+}
+
+template <typename T>
+cudaError_t launch_cell_vjp_direct(const MeshDesc& m, const T* U, const T* Fx, const T* Fy, const T* X, double alpha,
+                                   const T* Y, double beta, double c, T* out, cudaStream_t s) {
   const int nb = aux_blocks((long long)m.nx * m.ny);
   switch (m.limiter) {
     case LIM_MINMOD:
-      cell_vjp_kernel<T, LIM_MINMOD><<<nb, AUX_THREADS, 0, s>>>(m, U, Fx, Fy, X, T(alpha), Y, T(beta), T(c), out);
+      cell_vjp_direct_kernel<T, LIM_MINMOD><<<nb, AUX_THREADS, 0, s>>>(m, U, Fx, Fy, X, T(alpha), Y, T(beta), T(c), out);
       break;
     case LIM_SWEBY:
-      cell_vjp_kernel<T, LIM_SWEBY><<<nb, AUX_THREADS, 0, s>>>(m, U, Fx, Fy, X, T(alpha), Y, T(beta), T(c), out);
+      cell_vjp_direct_kernel<T, LIM_SWEBY><<<nb, AUX_THREADS, 0, s>>>(m, U, Fx, Fy, X, T(alpha), Y, T(beta), T(c), out);
       break;
     default:
-      cell_vjp_kernel<T, LIM_VANLEER><<<nb, AUX_THREADS, 0, s>>>(m, U, Fx, Fy, X, T(alpha), Y, T(beta), T(c), out);
+      cell_vjp_direct_kernel<T, LIM_VANLEER><<<nb, AUX_THREADS, 0, s>>>(m, U, Fx, Fy, X, T(alpha), Y, T(beta), T(c),
+                                                                       out);
   }
   return cudaGetLastError();
 }
@@ -133,9 +169,13 @@ cudaError_t launch_grad_prim(const MeshDesc& m, const T* U0, const T* lam, T* gq
   template cudaError_t launch_sums<T>(const MeshDesc&, const T*, double*, int, double*, cudaStream_t);      \
   template cudaError_t launch_species_to_cons<T>(const MeshDesc&, const T*, T*, cudaStream_t);           \
   template cudaError_t launch_cons_to_species<T>(const MeshDesc&, const T*, T*, cudaStream_t);           \
-  template cudaError_t launch_face_vjp<T>(const MeshDesc&, int, const T*, const T*, T*, cudaStream_t);        \
-  template cudaError_t launch_cell_vjp<T>(const MeshDesc&, const T*, const T*, const T*, const T*, double,    \
-                                          const T*, double, double, T*, cudaStream_t);                      \
+  template cudaError_t launch_adjoint_prep<T>(const MeshDesc&, const T*, T*, T*, T*, cudaStream_t);           \
+  template cudaError_t launch_face_vjp<T>(const MeshDesc&, int, const T*, const T*, const T*, T*, cudaStream_t); \
+  template cudaError_t launch_cell_vjp<T>(const MeshDesc&, const T*, const T*, const T*, const T*, const T*,     \
+                                          const T*, double, const T*, double, double, T*, cudaStream_t);         \
+  template cudaError_t launch_face_vjp_direct<T>(const MeshDesc&, int, const T*, const T*, T*, cudaStream_t);    \
+  template cudaError_t launch_cell_vjp_direct<T>(const MeshDesc&, const T*, const T*, const T*, const T*,        \
+                                                 double, const T*, double, double, T*, cudaStream_t);            \
   template cudaError_t launch_grad_prim<T>(const MeshDesc&, const T*, const T*, T*, cudaStream_t);
 
 }  // namespace lf
