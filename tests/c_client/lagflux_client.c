@@ -58,6 +58,11 @@ static int check_abi(void) {
   if (lf_init(&c, NULL, NULL) != LF_ERR_ARG) return fail("NULL out accepted");
   if (lf_step(NULL, NULL) != LF_ERR_ARG) return fail("lf_step(NULL)");
   if (lf_set_conservative(NULL, NULL, 0) != LF_ERR_ARG) return fail("lf_set_conservative(NULL)");
+  if (lf_set_tile_rows(NULL, 8) != LF_ERR_ARG) return fail("lf_set_tile_rows(NULL)");
+  if (lf_autotune(NULL, 1, NULL) != LF_ERR_ARG) return fail("lf_autotune(NULL)");
+  c = base_config();
+  c.tile_rows = -1;
+  if (lf_init(&c, NULL, &ctx) != LF_ERR_ARG) return fail("negative tile_rows accepted");
   if (strcmp(lf_status_string(LF_ERR_NONPHYSICAL), "LF_ERR_NONPHYSICAL") != 0) return fail("status string");
   lf_destroy(NULL);
   return 0;
@@ -89,6 +94,10 @@ static int check_run(void) {
   if (lf_conservation_sums(ctx, s0) != LF_OK) return fail("sums");
   int32_t done = 0;
   double t = 0.0;
+  int32_t rows = 0;
+  if (lf_autotune(ctx, 2, &rows) != LF_OK || rows < 4 || rows > 128) return fail("lf_autotune");
+  int32_t now = 0;
+  if (lf_get_tile_rows(ctx, &now) != LF_OK || now != rows) return fail("lf_get_tile_rows");
   if (lf_run(ctx, 0.0, 50, &done, &t) != LF_OK || done != 50 || !(t > 0.0)) return fail("lf_run");
   if (lf_conservation_sums(ctx, s1) != LF_OK) return fail("sums after");
   for (int l = 0; l < 4; ++l)
@@ -99,7 +108,7 @@ static int check_run(void) {
   lf_destroy(ctx);
   free(q);
   free(U);
-  printf("ok: 50 steps to t = %.6g, sums conserved\n", t);
+  printf("ok: 50 steps to t = %.6g (%d-row tiles), sums conserved\n", t, (int)rows);
   return 0;
 }
 
