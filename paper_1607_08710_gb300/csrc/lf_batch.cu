@@ -121,13 +121,24 @@ lf::MeshDesc problem_mesh(const lf_batch* b, int p) {
 // Work units for a tile height: problem by problem, row tile by row tile,
 // strip by strip, so that warps taking consecutive units share halo rows.
 lf_status build_units(lf_batch* b, int ty) {
-  const int out_cols = b->elem == 4 ? 60 : 28;  // output columns of a warp strip (CPL=2 FP32, CPL=1 FP64)
+  const int cols = b->elem == 4 ? 64 : 32;  // columns of a warp strip (CPL=2 FP32, CPL=1 FP64)
+  const int out_cols = cols - 4;           // its output columns
+  // Units of strips that lie inside their rows (the kernel's inner march)
+  // first, then the edge strips (the mapped march): warps take units in list
+  // order, so an SM runs mostly one of the two march bodies at a time instead
+  // of alternating between them (instruction-cache pressure).
   b->hunits.clear();
+  std::vector<lf::Unit> edge;
   for (int p = 0; p < b->nprob; ++p) {
     const lf::ProbDesc& d = b->hprobs[p];
     for (int j0 = 0; j0 < d.ny; j0 += ty)
-      for (int i0 = 0; i0 < d.nx; i0 += out_cols) b->hunits.push_back({p, i0, j0, std::min(j0 + ty, d.ny)});
+      for (int i0 = 0; i0 < d.nx; i0 += out_cols) {
+        const lf::Unit u{p, i0, j0, std::min(j0 + ty, d.ny)};
+        if (i0 - 2 >= 0 && i0 - 2 + cols <= d.nx) b->hunits.push_back(u);
+        else edge.push_back(u);
+      }
   }
+  b->hunits.insert(b->hunits.end(), edge.begin(), edge.end());
   if (b->hunits.size() > b->units_cap) {
     cudaFree(b->units);
     b->units = nullptr;
