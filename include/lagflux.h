@@ -91,7 +91,9 @@ enum { LF_TIME_HEUN = 2, LF_TIME_SSPRK3 = 3 };
 
 typedef struct lf_config {
   int32_t dim;       /* 1, 2 or 3 */
-  int32_t nx, ny;    /* cells per direction; ny == 1 when dim == 1 */
+  int32_t nx, ny;    /* cells per direction; ny == 1 when dim == 1.  A field plane
+                        (rows padded to 128 bytes) holds fewer than 2^31 elements:
+                        e.g. at most 46336 x 46340 cells in FP32 (LF_ERR_ARG otherwise) */
   int32_t limiter;   /* LF_LIMITER_* */
   int32_t bc;        /* LF_BC_* */
   int32_t precision; /* LF_FP64 or LF_FP32 */

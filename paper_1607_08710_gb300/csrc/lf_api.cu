@@ -45,7 +45,11 @@ const char* validate(const lf_config* c) {
   if (c->dim == 3 && c->nz < 1) return "nz must be >= 1 in 3D";
   if (c->nz < 0) return "nz must be >= 0";
   const long long nz = c->dim == 3 ? c->nz : 1;
-  if ((long long)c->nx * c->ny * nz > (1LL << 31)) return "mesh larger than 2^31 cells";
+  // Rows are padded to 128 bytes and element offsets inside a field plane are
+  // 32-bit in the kernels, so the padded plane must stay below 2^31 elements.
+  const long long align = c->precision == LF_FP32 ? 32 : 16;
+  if ((c->nx + align - 1) / align * align * c->ny * nz >= (1LL << 31))
+    return "mesh too large: a field plane (rows padded to 128 bytes) must have fewer than 2^31 elements";
   if (c->dim == 3 && (!(c->zmax > c->zmin) || !std::isfinite(c->zmax - c->zmin))) return "need zmin < zmax";
   if (c->tile_rows < 0 || c->tile_rows > 4096) return "tile_rows must be in 0 .. 4096";
   if (c->limiter < 0 || c->limiter > 2) return "unknown limiter";

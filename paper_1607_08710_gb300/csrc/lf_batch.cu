@@ -83,6 +83,8 @@ const char* check_problem(const lf_config* c, const lf_config* c0) {
   if (c->dim != 2) return "batched problems must be 2D";
   if (c->nx < 1 || c->ny < 1) return "nx and ny must be >= 1";
   if ((long long)c->nx * c->ny > (1LL << 30)) return "problem larger than 2^30 cells";
+  // element offsets inside a problem's planes are 32-bit (rows padded to 128 bytes)
+  if ((c->nx + 31LL) / 32 * 32 * c->ny >= (1LL << 31)) return "problem plane (rows padded) of 2^31 or more elements";
   if (c->limiter < 0 || c->limiter > 2 || c->bc < 0 || c->bc > 1 || c->riemann < 0 || c->riemann > 1)
     return "unknown limiter, boundary condition or interface solver";
   if (c->precision != LF_FP64 && c->precision != LF_FP32) return "unknown precision";

@@ -77,6 +77,25 @@ def test_init_rejects_bad_config_without_gpu(lib, field, value):
     assert b"invalid configuration" in lib.lf_last_error(None)
 
 
+@pytest.mark.parametrize("dims,precision", [((46340, 46340, 1), "fp32"), ((46340, 46340, 1), "fp64"),
+                                            ((46337, 46340, 1), "fp32"), ((2048, 1024, 1025), "fp32"),
+                                            ((1, 2**30, 1), "fp32")])
+def test_init_rejects_meshes_past_the_32_bit_plane_without_gpu(lib, dims, precision):
+    """Element offsets inside a field plane are 32-bit in the kernels and rows
+    are padded to 128 bytes: a mesh whose padded plane reaches 2^31 elements
+    is refused before anything touches a GPU, even when its cell count is
+    below 2^31 (46340^2 cells = 2,147,395,600 < 2^31, but the padded FP32
+    plane of 46368 x 46340 elements is not)."""
+    nx, ny, nz = dims
+    kw = dict(nx=nx, ny=ny, precision=precision)
+    if nz > 1:
+        kw.update(nz=nz, dim=3)
+    cfg = lib.Config(**kw).to_c()
+    h = ctypes.c_void_p()
+    assert lib.lf_init(ctypes.byref(cfg), None, ctypes.byref(h)) == lib.LF_ERR_ARG
+    assert b"2^31" in lib.lf_last_error(None)
+
+
 @pytest.mark.parametrize("field,value", [("zmax", 0.0), ("nz", 0), ("nspecies", 3)])
 def test_init_rejects_bad_3d_config_without_gpu(lib, field, value):
     cfg = lib.Config(nx=8, ny=8, nz=8, dim=3).to_c()
@@ -133,3 +152,11 @@ def test_product_package_never_imports_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle\b", text, flags=re.M), f
                 assert "lagflux_oracle" not in text and "liblagflux_oracle" not in text, f
+
+
+def test_batch_init_rejects_problems_past_the_32_bit_plane_without_gpu(lib):
+    cfgs = (lib.lf_config * 2)(lib.Config(nx=64, ny=64, precision="fp32").to_c(),
+                               lib.Config(nx=1, ny=2**26 + 1, precision="fp32").to_c())
+    h = ctypes.c_void_p()
+    assert lib.lf_batch_init(cfgs, 2, None, ctypes.byref(h)) == lib.LF_ERR_ARG
+    assert h.value is None
