@@ -134,6 +134,26 @@ def smooth_wave_1d(nx: int, t: float = 0.0) -> Primitive:
     return Primitive(rho, one.copy(), np.zeros((1, nx)), one.copy())
 
 
+def kelvin_helmholtz_profiles(nx: int, ny: int | None = None, seed: int = 0, amplitude: float = 0.01,
+                              modes: int = 8):
+    """The shear layer of kelvin_helmholtz as its 1D profiles: (rho_y, u_y,
+    v_x, p) with rho_y, u_y of shape (ny,) (functions of y), v_x of shape
+    (nx,) (a function of x) and the constant p; rho(j, i) = rho_y[j],
+    u(j, i) = u_y[j], v(j, i) = v_x[i].  For meshes too large to lay out on
+    the host."""
+    ny = nx if ny is None else ny
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0.0, 1.0, modes)
+    phi = rng.uniform(0.0, 2.0 * math.pi, modes)
+    x = cell_centres(nx)
+    y = cell_centres(ny)
+    k = np.arange(1, modes + 1)[:, None]
+    S = (a[:, None] * np.sin(2.0 * math.pi * k * x[None, :] + phi[:, None])).sum(axis=0)
+    vrow = amplitude * S / np.max(np.abs(S))
+    inside = np.abs(y - 0.5) < 0.25
+    return np.where(inside, 2.0, 1.0), np.where(inside, 0.5, -0.5), vrow, 2.5
+
+
 def kelvin_helmholtz(nx: int, ny: int | None = None, seed: int = 0, amplitude: float = 0.01,
                      modes: int = 8) -> Primitive:
     """Shear layer: rho = 2, u = +0.5 inside |y - 0.5| < 0.25; rho = 1, u = -0.5 outside; p = 2.5.
@@ -143,20 +163,11 @@ def kelvin_helmholtz(nx: int, ny: int | None = None, seed: int = 0, amplitude: f
     numpy's default generator.
     """
     ny = nx if ny is None else ny
-    rng = np.random.default_rng(seed)
-    a = rng.uniform(0.0, 1.0, modes)
-    phi = rng.uniform(0.0, 2.0 * math.pi, modes)
-    x = cell_centres(nx)
-    y = cell_centres(ny)[:, None]
-    k = np.arange(1, modes + 1)[:, None]
-    S = (a[:, None] * np.sin(2.0 * math.pi * k * x[None, :] + phi[:, None])).sum(axis=0)
-    vrow = amplitude * S / np.max(np.abs(S))
-    inside = np.abs(y - 0.5) < 0.25
-    rho = np.where(inside, 2.0, 1.0) * np.ones((1, nx))
-    u = np.where(inside, 0.5, -0.5) * np.ones((1, nx))
-    v = np.broadcast_to(vrow[None, :], (ny, nx)).copy()
-    p = np.full((ny, nx), 2.5)
-    return Primitive(rho, u, v, p)
+    rho_y, u_y, v_x, p = kelvin_helmholtz_profiles(nx, ny, seed, amplitude, modes)
+    rho = np.broadcast_to(rho_y[:, None], (ny, nx)).copy()
+    u = np.broadcast_to(u_y[:, None], (ny, nx)).copy()
+    v = np.broadcast_to(v_x[None, :], (ny, nx)).copy()
+    return Primitive(rho, u, v, np.full((ny, nx), p))
 
 
 def smooth_perturbation(nx: int, ny: int | None = None, seed: int = 0, modes: int = 4) -> np.ndarray:

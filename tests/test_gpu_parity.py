@@ -282,6 +282,59 @@ def test_full_size_8192_sampled_cells(precision):
     s.close()
 
 
+def test_maximum_fp32_mesh_sampled_cells():
+    """The largest FP32 mesh lf_init accepts: 46336 x 46340 cells, whose field
+    plane (rows padded to 128 bytes) is just under 2^31 elements, where the
+    kernels' 32-bit in-plane offsets peak (69 GB for the two states).  The
+    periodic Kelvin-Helmholtz layer is built on the device from its 1D
+    profiles; one CFL step is checked at sampled cells, the last rows and
+    columns among them, against the oracle on patches, and the GPU dt against
+    the oracle's CFL dt: the layer is a product of a y-profile (rho, u) and
+    an x-profile (v), so a two-row mesh with the same dx and dy holding one
+    row of each kind has the dt of the whole mesh."""
+    nx, ny = 46336, 46340
+    free, _ = torch.cuda.mem_get_info()
+    if free < 115e9:
+        pytest.skip("needs about 105 GB of free device memory")
+    rho_y, u_y, v_x, p = inputs.kelvin_helmholtz_profiles(nx, ny, seed=0)
+    kw = dict(limiter="vanleer", bc="periodic", cfl=0.45)
+    s = LagrangeFlux(Config(nx=nx, ny=ny, precision="fp32", **kw))
+    f32 = dict(device="cuda", dtype=torch.float32)
+    planes = [torch.as_tensor(rho_y, **f32)[:, None].expand(ny, nx).contiguous(),
+              torch.as_tensor(u_y, **f32)[:, None].expand(ny, nx).contiguous(),
+              torch.as_tensor(v_x, **f32)[None, :].expand(ny, nx).contiguous(),
+              torch.full((ny, nx), p, **f32)]
+    s.set_primitive(*planes)
+    del planes
+    torch.cuda.empty_cache()
+    U = torch.empty((4, ny, nx), **f32)
+    s.get_state(U)
+    rng = np.random.default_rng(1)
+    samples = [(0, 0), (nx - 1, ny - 1), (0, ny - 1), (nx - 1, 0), (nx - 3, ny - 2), (nx // 2, ny // 4 + 1)]
+    samples += [tuple(v) for v in zip(rng.integers(0, nx, 14), rng.integers(0, ny, 14))]
+    r = 6
+    patches = {}
+    for ci, cj in samples:
+        ii = torch.as_tensor(np.arange(ci - r, ci + r + 1) % nx, device="cuda")
+        jj = torch.as_tensor(np.arange(cj - r, cj + r + 1) % ny, device="cuda")
+        patches[(ci, cj)] = U[:, jj][:, :, ii].double().cpu().numpy()
+    rows = U[:, [0, ny // 2]].double().cpu().numpy()  # one row outside the layer, one inside
+    dt = s.step(return_dt=True)
+    oc = O.OracleConfig(nx=nx, ny=2, ly=2.0 / ny, **kw)
+    assert dt == pytest.approx(O.cfl_dt(oc, rows), rel=1e-6)
+    s.get_state(U)
+    okw = {k: v for k, v in kw.items() if k != "bc"}
+    for ci, cj in samples:
+        pc = O.OracleConfig(nx=2 * r + 1, ny=2 * r + 1, lx=(2 * r + 1) / nx, ly=(2 * r + 1) / ny,
+                            bc="transmissive", **okw)
+        ref = O.run(pc, patches[(ci, cj)], 1, dts=[dt]).U[:, r, r]
+        got = U[:, cj, ci].double().cpu().numpy()
+        assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max(), (ci, cj, got, ref)
+    s.close()
+    del U
+    torch.cuda.empty_cache()
+
+
 def test_run_graph_replay_equals_direct_steps():
     # lf_run issues steps as replays of a recorded 32-step CUDA graph plus a
     # direct remainder; lf_step launches directly.  Same kernels, same order:
