@@ -22,6 +22,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -179,11 +180,21 @@ class ClockSampler:
 KERNEL_SOURCES = ("lf_device.cuh", "lf_stage.cuh", "lf_internal.h", "lf_kernels_f32.cu", "lf_kernels_f64.cu")
 
 
-def kernel_source_hash() -> str:
-    """Hash of the device code that the stage kernels are compiled from."""
+def code_text(src: str) -> str:
+    """C++/CUDA source without comments and with whitespace collapsed: the
+    part of a file that decides what the compiler builds."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
+def kernel_source_hash(root: str = ROOT) -> str:
+    """Hash of the device code that the stage kernels are compiled from
+    (comments and layout excluded, so a counter capture stays tied to the
+    code it measured)."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_1607_08710_gb300", "csrc", f), "rb").read())
+        h.update(code_text(open(os.path.join(root, "paper_1607_08710_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -15,16 +15,19 @@
 // in registers: primitives of three rows, y-slopes and the flux through the
 // face below, each in three slots indexed by row mod 3.  The march is
 // unrolled by three so the slots are compile-time register names and nothing
-// is copied from row to row.  The next row is prefetched one iteration ahead;
-// the conservative values of the row being updated are re-read (an L1 hit)
-// rather than carried.  Every primitive, slope and face flux is computed once
-// per cell, up to the 4 halo columns of a strip and the 2 halo rows below and
-// above a tile.
+// is copied from row to row.  Rows are staged by cp.async into a per-warp
+// shared-memory ring four rows ahead; the conservative values of the row
+// being updated are read back from the ring rather than carried.  Every
+// primitive, slope and face flux is computed once per cell, up to the 4 halo
+// columns of a strip and the 2 halo rows below and above a tile.  The tile
+// height is a launch parameter (MeshDesc::ty); strips that lie inside their
+// rows run a march without per-lane copy and store choices.
 //
 // Memory safety.  Every load index is mapped into [0, nx) x [0, ny) by the
 // boundary condition (clamp or wrap); vector loads/stores are used only when
 // both cells of the pair are inside the row; stores are issued only for
-// output cells (column < nx, row < ny).
+// output cells (column < nx, row < ny).  In-plane element offsets are 32-bit:
+// lf_init refuses meshes whose padded plane reaches 2^31 elements.
 #pragma once
 
 #include "lf_device.cuh"
