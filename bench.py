@@ -455,7 +455,10 @@ def run_ours(args, dist):
     kname = {k: v % ("float" if prec == "fp32" else "double") for k, v in kname.items()}
     traffic = measured_traffic(kname[dom], cells)
     roofline = {"bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": peak, "unit": "GB/s",
-                "frac": kernels[dom]["gbs"] / peak, "traffic": traffic, "kernel": kname[dom],
+                "frac": kernels[dom]["gbs"] / peak, "traffic": traffic,
+                # ncu-measured DRAM bytes of a launch over its live duration
+                "traffic_frac": None if traffic is None else traffic / (kernels[dom]["avg_ms"] / 1e3) / 1e9 / peak,
+                "kernel": kname[dom],
                 "peak_kind": f"{peak_kind} copy bandwidth",
                 "step_frac": (sum(BYTES_PER_CELL[(k, prec)] for k in ("stage0", "stage1")) * cells * args.steps / t_local
                               / 1e9) / peak}
