@@ -68,6 +68,7 @@ const char* check_config(const lf_config* c) {
   if (c->limiter < 0 || c->limiter > 2 || c->bc < 0 || c->bc > 1 || c->riemann < 0 || c->riemann > 1)
     return "unknown limiter, boundary condition or interface solver";
   if (c->precision != LF_FP64 && c->precision != LF_FP32) return "unknown precision";
+  if (c->tile_rows < 0 || c->tile_rows > 4096) return "tile_rows must be in 0 .. 4096";
   if (c->device < 0 || c->device >= kMaxDevices) return "device out of range";
   if (!(c->xmax > c->xmin) || (c->dim == 2 && !(c->ymax > c->ymin))) return "empty domain";
   if (!(c->gamma > 1.0 && c->gamma <= 3.0) || !(c->cfl > 0.0 && c->cfl <= 1.0)) return "gamma or cfl out of range";
@@ -129,6 +130,11 @@ extern "C" lf_status lf_step_noalloc(const lf_config* cfg, const void* U_in, voi
     m.rdy = cfg->dim == 2 ? cfg->ny / (cfg->ymax - cfg->ymin) : 0.0;
     // dense planes: vector access only when every row and plane start stays aligned
     m.vec = (cfg->nx % 2 == 0) && ((uintptr_t)U_in % 16 == 0) && ((uintptr_t)U_out % 16 == 0);
+    if (cfg->dim == 2) {  // the tile height of lf_init contexts (or the configured one)
+      int sms = 0;
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess) sms = 0;
+      m.ty = cfg->tile_rows > 0 ? cfg->tile_rows : lf::auto_tile_rows(m, cfg->precision == LF_FP32 ? 2 : 1, sms);
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     lf::Scalars* sc = static_cast<lf::Scalars*>(base);
     void* ustar = static_cast<unsigned char*>(base) + kScalarBytes;
