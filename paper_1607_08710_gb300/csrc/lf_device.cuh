@@ -198,12 +198,22 @@ __device__ __forceinline__ void lagrange_flux(const Phys<V>& P, const V qL[NF], 
     //   p* = p_L + w (p_R - p_L) - rho_R w a (u_R - u_L)
     //   u* = u_R - w (u_R - u_L) - (p_R - p_L) / ((rho_L + rho_R) a).
     const V a2 = P.gamma * max_quotient(pL, rL, pR, rR);
-    V a, ia;
-    Ar<V>::sqrt_and_rsqrt(a2, a, ia);
-    const V irs = Ar<V>::rcp(rL + rR);
+    V a, irs, irs_ia;  // a, 1/(rho_L + rho_R), 1/((rho_L + rho_R) a)
+    if constexpr (LaneT<V>::N == 1 && sizeof(typename LaneT<V>::S) == 8) {
+      // FP64: both reciprocals from one IEEE division (a division is a long
+      // instruction sequence on the FP64 pipe)
+      a = Ar<V>::sqrt_(a2);
+      irs_ia = Ar<V>::rcp(a * (rL + rR));
+      irs = a * irs_ia;
+    } else {
+      V ia;
+      Ar<V>::sqrt_and_rsqrt(a2, a, ia);
+      irs = Ar<V>::rcp(rL + rR);
+      irs_ia = irs * ia;
+    }
     const V w = rL * irs, dp = pR - pL;
     pstar = fma_(rR * w * a, ndu, fma_(w, dp, pL));
-    ustar = fma_(ndp, irs * ia, fma_(w, ndu, unR));
+    ustar = fma_(ndp, irs_ia, fma_(w, ndu, unR));
   } else {
     // acoustic solver with Z_k = rho_k c_k
     const V ZL = rL * Ar<V>::sqrt_(P.gamma * Ar<V>::div(pL, rL));

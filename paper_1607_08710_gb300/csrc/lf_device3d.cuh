@@ -35,12 +35,20 @@ __device__ __forceinline__ void lagrange_flux3(const Phys<V>& P, const V qL[NF],
   V pstar, ustar;
   if (P.riemann == RIEMANN_MAXC) {
     const V a2 = P.gamma * max_quotient(pL, rL, pR, rR);
-    V a, ia;
-    Ar<V>::sqrt_and_rsqrt(a2, a, ia);
-    const V irs = Ar<V>::rcp(rL + rR);
+    V a, irs, irs_ia;  // as lagrange_flux
+    if constexpr (LaneT<V>::N == 1 && sizeof(typename LaneT<V>::S) == 8) {
+      a = Ar<V>::sqrt_(a2);
+      irs_ia = Ar<V>::rcp(a * (rL + rR));
+      irs = a * irs_ia;
+    } else {
+      V ia;
+      Ar<V>::sqrt_and_rsqrt(a2, a, ia);
+      irs = Ar<V>::rcp(rL + rR);
+      irs_ia = irs * ia;
+    }
     const V w = rL * irs, dp = pR - pL;
     pstar = fma_(rR * w * a, ndu, fma_(w, dp, pL));
-    ustar = fma_(ndp, irs * ia, fma_(w, ndu, unR));
+    ustar = fma_(ndp, irs_ia, fma_(w, ndu, unR));
   } else {
     const V ZL = rL * Ar<V>::sqrt_(P.gamma * Ar<V>::div(pL, rL));
     const V ZR = rR * Ar<V>::sqrt_(P.gamma * Ar<V>::div(pR, rR));
