@@ -21,9 +21,11 @@
 // Memory.  The input planes (the CTA's rows plus halo rows, all fields) are
 // staged into a shared ring four planes deep by cp.async, each warp copying
 // its own row and warps 0-3 one halo row each; the U^n rows of the later
-// stages into a two-plane ring.
+// stages into a two-plane ring.  CTAs whose strip lies inside the rows make
+// these copies in one CTA-uniform branch, one vector copy per field and row.
 // One commit group per plane: at the top of a step the group issued one step
-// earlier is complete and a barrier makes it visible to the whole CTA.
+// earlier is complete and a barrier makes it visible to the whole CTA.  The
+// planes per z-tile are a launch parameter (Mesh3Desc::tz).
 // Every global index is mapped into the mesh by the boundary condition, and
 // only output cells (column < nx, row < ny, plane < nz) are stored.
 #pragma once
