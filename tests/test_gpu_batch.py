@@ -18,7 +18,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-from paper_1607_08710_gb300.lagflux import Config, LagrangeFluxBatch, LagrangeFluxError  # noqa: E402
+from paper_1607_08710_gb300.lagflux import Config, LagrangeFlux, LagrangeFluxBatch, LagrangeFluxError  # noqa: E402
 
 SIZES = [(37, 61), (64, 64), (100, 33), (1, 5), (130, 70), (17, 200), (61, 61), (3, 2)]
 
@@ -160,3 +160,27 @@ def test_full_size_512_problems_sampled():
         ref = O.run(oc, O.prim_to_cons(oc, prims[p]), 3)
         assert max(field_errors(got, ref.U)) <= 2e-5, (p, field_errors(got, ref.U))
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("bc,kind", [("transmissive", "quadrant"), ("periodic", "kh")])
+def test_batch_equals_single_meshes_bitwise(precision, bc, kind):
+    """A problem of a batch runs the same march (inner-strip or mapped, the
+    same arithmetic) with its own CFL dt as the same mesh in its own context,
+    so after the same steps the states agree bit for bit -- whatever the
+    order in which the persistent kernel's warps took the units."""
+    sizes = SIZES + [(300, 131)]
+    steps = 17
+    b, prims = make_batch(sizes, precision, bc=bc, kind=kind)
+    b.run(steps)
+    got = states(b, sizes)
+    b.close()
+    tdt = torch.float64 if precision == "fp64" else torch.float32
+    for p, (nx, ny) in enumerate(sizes):
+        s = LagrangeFlux(Config(nx=nx, ny=ny, precision=precision, limiter="vanleer", bc=bc, cfl=0.45))
+        q = torch.from_numpy(prims[p]).to("cuda", tdt)
+        s.set_primitive(q[0], q[1], q[2], q[3])
+        s.run(max_steps=steps)
+        single = s.get_state().astype(np.float64)
+        s.close()
+        assert np.array_equal(got[p], single), f"problem {p} ({nx}x{ny})"
