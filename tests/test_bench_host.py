@@ -56,3 +56,26 @@ def test_reference_arm_prints_one_json_line():
     assert j["higher_is_better"] is True and j["steps"] == 2 and j["warmup"] == 1
     assert j["cpu_baseline"]["kind"] == "oracle" and j["cpu_baseline"]["cores"] == 1
     assert j["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_kernel_source_hash_follows_code_not_comments(tmp_path):
+    """The DRAM-traffic and FP64-flop counters under profiles/ are used only
+    while this hash matches the one they were captured with: a comment or
+    layout edit keeps it, any code edit changes it."""
+    import shutil
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    csrc = os.path.join("paper_1607_08710_gb300", "csrc")
+    os.makedirs(tmp_path / csrc)
+    for f in bench.KERNEL_SOURCES:
+        shutil.copy(os.path.join(ROOT, csrc, f), tmp_path / csrc / f)
+    base = bench.kernel_source_hash(str(tmp_path))
+    assert base == bench.kernel_source_hash()
+    path = tmp_path / csrc / bench.KERNEL_SOURCES[0]
+    text = path.read_text()
+    path.write_text("// an added comment\n/* and a block\n   comment */\n" + text.replace("\n", "\n\n", 3))
+    assert bench.kernel_source_hash(str(tmp_path)) == base
+    path.write_text(text + "\nnamespace lf { inline int extra_code() { return 1; } }\n")
+    assert bench.kernel_source_hash(str(tmp_path)) != base
