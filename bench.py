@@ -60,10 +60,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--e2e-run-steps", type=int, default=100)
     ap.add_argument("--profile-steps", type=int, default=20)
-    ap.add_argument("--cpu-sample-size", type=int, default=1024)
-    ap.add_argument("--cpu-sample-steps", type=int, default=8)
+    ap.add_argument("--ref-size", type=int, default=0,
+                    help="mesh side of the --impl reference arm (0: --size, the benchmark's own mesh)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the measured FMA peaks (and the ALU rooflines)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-rk3", action="store_true")
@@ -83,12 +84,13 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(args):
-    return {"workload": f"periodic Kelvin-Helmholtz shear layer {args.size}x{args.size}",
-            "nx": args.size, "ny": args.size, "gamma": 1.4, "limiter": "van Leer", "cfl": 0.45,
+def workload_config(args, n=None):
+    n = n or args.size
+    return {"workload": f"periodic Kelvin-Helmholtz shear layer {n}x{n}",
+            "nx": n, "ny": n, "gamma": 1.4, "limiter": "van Leer", "cfl": 0.45,
             "bc": "periodic", "riemann": "eqs. 13-14, a = max(c_L, c_R)", "seed": 0,
             "l2_policy": "inputs larger than L2 (state %.2f GB vs 129 MB L2), no flush" %
-                         (4 * args.size * args.size * (4 if args.precision == "fp32" else 8) / 1e9)}
+                         (4 * n * n * (4 if args.precision == "fp32" else 8) / 1e9)}
 
 
 # ---------------------------------------------------------------------------
@@ -215,20 +217,62 @@ def measured_traffic(kernel: str, cells: int):
         return None
 
 
-def fp64_alu_roofline(stage_ms, cells):
-    """FP64 ALU roofline of the FP64 corrector: executed FP64 flops per cell
-    (ncu counts of the committed capture, valid for the current kernel
-    sources) x cells / live kernel time, against the FP64 FMA peak."""
-    path = os.path.join(ROOT, "profiles", "fp64_flops.json")
+def algorithmic_flops(workload: str = "kh2d"):
+    """The method's flops per cell (predictor, corrector, step) from the
+    oracle's op count stored in profiles/algorithmic_flops.json (written by
+    oracle/count_flops.py); None when absent."""
+    path = os.path.join(ROOT, "profiles", "algorithmic_flops.json")
     if not os.path.exists(path):
         return None
-    d = json.load(open(path))
-    if d.get("source_hash") != kernel_source_hash():
+    try:
+        return json.load(open(path))["workloads"][workload]["flops_per_cell"]
+    except (KeyError, ValueError):
         return None
+
+
+def alu_peaks(device: int):
+    """Measured FMA throughput (lf_measure_peak) of FP64, FP32 and paired FP32,
+    with the SM clock sampled while the chains run."""
+    from paper_1607_08710_gb300.lagflux import measure_peak
+
+    clocks = ClockSampler(None)
+    clocks.start()
+    res = {k: measure_peak(k, device, 50.0) for k in ("fp64", "fp32", "fp32_paired")}
+    res["clocks"] = clocks.stop()
+    res["unit"] = "TFLOP/s"
+    res["how"] = "lf_measure_peak: 8 independent FMA chains per thread, 8 CTAs x 256 threads per SM, best of 3 launches"
+    return res
+
+
+def fp64_alu_roofline(stage_ms, cells, alu):
+    """FP64 ALU roofline of the FP64 corrector: the method's algorithmic flops
+    per cell (oracle op count) x cells / live kernel time, against the measured
+    FP64 FMA peak; beside it the FP64 flops the kernel executes (ncu count of
+    the committed capture, when it matches the current kernel sources), which
+    include the Newton sequences of the divisions and square roots."""
     k = "stage2d_kernel<double, VANLEER, corrector>"
-    achieved = d["kernels"][k]["fp64_flops_per_cell"] * cells / (stage_ms[1] / 1e3) / 1e12
-    return {"bound": "alu", "kernel": k, "achieved": achieved, "peak": d["peak_tflops"], "unit": "TFLOP/s",
-            "frac": achieved / d["peak_tflops"], "peak_kind": "derived: " + d["peak_derivation"]}
+    alg = algorithmic_flops()
+    if alg is None or not alu:
+        return None
+    t = stage_ms[1] / 1e3
+    peak = alu["fp64"]
+    achieved = alg["corrector"] * cells / t / 1e12
+    sm = alu.get("clocks", {}).get("sm_mhz")
+    roof = {"bound": "alu", "kernel": k, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "flops_per_cell": alg["corrector"],
+            "flops_kind": "algorithmic: oracle op count of the method, each add, multiply, divide and root one flop "
+                          f"({alg['div_sqrt']['corrector']:.1f} of them divisions or roots; "
+                          "profiles/algorithmic_flops.json)",
+            "peak_kind": f"measured: lf_measure_peak DFMA chains (SM clock {sm} MHz)"}
+    path = os.path.join(ROOT, "profiles", "fp64_flops.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        if d.get("source_hash") == kernel_source_hash():
+            ex = d["kernels"][k]["fp64_flops_per_cell"]
+            roof["executed"] = {"flops_per_cell": ex, "achieved": ex * cells / t / 1e12,
+                                "frac": ex * cells / t / 1e12 / peak,
+                                "source": "ncu dadd + dmul + 2 dfma per cell (" + d["capture"] + ")"}
+    return roof
 
 
 def peaks():
@@ -239,50 +283,95 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def cpu_baseline(args):
-    """The CPU oracle as it stands (single thread), on a bounded sample of the
-    same workload: the same shear-layer generator on a smaller periodic mesh."""
-    from oracle import oracle as O
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+CPU_SAMPLES = {  # the oracle's timing samples: (generator, bc, mesh side, steps)
+    "C1": ("four-quadrant Riemann problem (seed 0)", "transmissive", 2048, 10),
+    "C2": ("periodic Kelvin-Helmholtz shear layer (seed 0)", "periodic", 1024, 20),
+}
+
+
+def time_oracle(O, key, n=None, steps=None):
+    """Seconds and steps of one oracle run of sample `key` (the loaded build)."""
     from paper_1607_08710_gb300 import inputs
 
-    n, steps = args.cpu_sample_size, args.cpu_sample_steps
-    oc = O.OracleConfig(nx=n, ny=n, limiter="vanleer", bc="periodic", cfl=0.45)
-    U0 = O.prim_to_cons(oc, inputs.kelvin_helmholtz(n, n, seed=0).stack())
-    O.run(oc, U0, 1)  # warm the library
+    what, bc, n0, s0 = CPU_SAMPLES[key]
+    n, steps = n or n0, steps or s0
+    oc = O.OracleConfig(nx=n, ny=n, limiter="vanleer", bc=bc, cfl=0.45)
+    q = inputs.quadrant(n, n, seed=0) if key == "C1" else inputs.kelvin_helmholtz(n, n, seed=0)
+    U0 = O.prim_to_cons(oc, q.stack())
     t0 = time.perf_counter()
     r = O.run(oc, U0, steps)
-    el = time.perf_counter() - t0
-    return {"value": n * n * r.steps / el, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle, periodic Kelvin-Helmholtz {n}x{n}, {r.steps} steps ({el:.1f} s), single thread",
-            "seconds": el}
+    return time.perf_counter() - t0, r.steps, n
+
+
+def cpu_baseline(args):
+    """The CPU oracle as it stands on bounded samples of the workloads: C1
+    (2048^2 four-quadrant problem, 10 steps) and C2 (1024^2 periodic shear
+    layer, 20 steps), each single-threaded (the plain build) and on all host
+    cores (the same source built with OpenMP, same bits).  The headline is C2
+    (the benchmark's generator on a smaller mesh) on all cores."""
+    from oracle import oracle as O
+
+    cores = host_cores()
+    runs = []
+    for key in ("C1", "C2"):
+        el, steps, n = time_oracle(O, key)
+        runs.append({"sample": key, "mesh": f"{n}x{n}", "steps": steps, "threads": 1, "seconds": el,
+                     "value": n * n * steps / el})
+    with O.use_library(O.build_omp()):
+        threads = O.threads(cores)
+        for key in ("C1", "C2"):
+            time_oracle(O, key, n=256, steps=1)  # start the thread pool
+            el, steps, n = time_oracle(O, key)
+            runs.append({"sample": key, "mesh": f"{n}x{n}", "steps": steps, "threads": threads, "seconds": el,
+                         "value": n * n * steps / el})
+    head = runs[-1]
+    return {"value": head["value"], "unit": METRIC, "cores": threads, "kind": "oracle",
+            "sample": f"FP64 oracle (OpenMP build, {threads} threads), periodic Kelvin-Helmholtz "
+                      f"{head['mesh']}, {head['steps']} steps ({head['seconds']:.1f} s)",
+            "single_thread": runs[1]["value"], "runs": runs,
+            "samples": {k: f"{v[0]}, {v[2]}x{v[2]}, {v[3]} steps, {v[1]}" for k, v in CPU_SAMPLES.items()}}
 
 
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ---------------------------------------------------------------------------
 def run_reference(args, dist):
+    """The CPU oracle (OpenMP build, all host cores) on the benchmark's own
+    workload: W warm-up steps, then K timed Heun steps of the 8192^2 periodic
+    shear layer (about 4 s per step on 16 Grace cores).  --ref-size runs a
+    smaller mesh of the same generator, and the config line then names it."""
     if dist.rank != 0:
         return
     from oracle import oracle as O
     from paper_1607_08710_gb300 import inputs
 
-    n = args.cpu_sample_size
+    n = args.ref_size or args.size
     oc = O.OracleConfig(nx=n, ny=n, limiter="vanleer", bc="periodic", cfl=0.45)
     U = O.prim_to_cons(oc, inputs.kelvin_helmholtz(n, n, seed=0).stack())
-    for _ in range(args.warmup):
-        U = O.run(oc, U, 1).U
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        U = O.run(oc, U, 1).U
-    el = time.perf_counter() - t0
-    v = n * n * args.steps / el
-    cfg = workload_config(args)
-    sample = f"FP64 oracle, each step one Heun step of the same shear layer on {n}x{n} cells, single thread"
+    with O.use_library(O.build_omp()):
+        threads = O.threads(host_cores())
+        if args.warmup > 0:
+            U = O.run(oc, U, args.warmup).U
+        t0 = time.perf_counter()
+        r = O.run(oc, U, args.steps)
+        el = time.perf_counter() - t0
+    v = n * n * r.steps / el
+    cfg = workload_config(args, n)
+    sample = (f"FP64 oracle (OpenMP build, {threads} threads), {r.steps} Heun steps of the periodic "
+              f"Kelvin-Helmholtz shear layer on {n}x{n} cells after {args.warmup} warm-up steps")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-        "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+        "steps": r.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(r.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": cfg,
+        "cpu_baseline": {"value": v, "unit": METRIC, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -324,6 +413,40 @@ def run_batched(args, dist, dev):
             "cells": cells, "steps": args.batch_steps, "ms_per_step": 1e3 * t / args.batch_steps,
             "tile_rows": rows, "graph": True, "launches_per_step": 4,
             "workload": "four-quadrant Riemann problems, sides log-uniform in [64, 1024], seeds 0..P-1"}
+
+
+def fd_at_literal_state(s, q, gq, dts, rho_target, n, ndir=4):
+    """Central finite differences of J along seeded smooth directions in
+    (rho0, p0) at the literal shear layer, replaying the frozen dt sequence,
+    against <grad, d> of the adjoint.  The layer is piecewise constant, so
+    every slope starts on the limiter's kink and every max(c_L, c_R) inside a
+    layer is a tie: J is only directionally differentiable there (a
+    non-smooth point), and the two need not agree.  Reported, not a check."""
+    import torch
+
+    from paper_1607_08710_gb300 import inputs
+
+    def J(qq):
+        s.set_primitive(qq[0], qq[1], qq[2], qq[3])
+        for dt in dts:
+            s.step_fixed(float(dt))
+        U = torch.empty_like(qq)
+        s.get_state(U)
+        return float(((U[0] - rho_target) ** 2).sum())
+
+    errs = {}
+    for h in (1e-6, 1e-7):
+        e = []
+        for k in range(ndir):
+            d = torch.zeros_like(q)
+            d[0] = torch.from_numpy(inputs.smooth_perturbation(n, n, seed=1000 + 2 * k)).to(q)
+            d[3] = torch.from_numpy(inputs.smooth_perturbation(n, n, seed=1001 + 2 * k)).to(q)
+            ad = float((gq * d).sum())
+            fd = (J(q + h * d) - J(q - h * d)) / (2 * h)
+            e.append(abs(fd - ad) / abs(ad))
+        errs[f"h={h:g}"] = e
+    return {"label": "non-smooth point (literal shear layer, no background)", "directions": ndir,
+            "relative_error_per_direction": errs}
 
 
 def run_adjoint(args, dev):
@@ -369,7 +492,7 @@ def run_adjoint(args, dev):
             s.set_primitive(q[0], q[1], q[2], q[3])
             torch.cuda.synchronize()
             ev[2].record()
-            s.adjoint_forward(nsteps)
+            dts = s.adjoint_forward(nsteps)
             ev[3].record()
             s.get_state(UT)
             lam[0] = 2.0 * (UT[0] - rho_target)
@@ -383,10 +506,12 @@ def run_adjoint(args, dev):
         t_fwd = ev[2].elapsed_time(ev[3]) / 1e3
         t_bwd = e_b0.elapsed_time(ev[4]) / 1e3
         assert bool(torch.isfinite(gq).all())
-        s.close()
         res[prec] = {"value": cells * nsteps / (t_fwd + t_bwd), "forward_ms": 1e3 * t_fwd,
                      "backward_ms": 1e3 * t_bwd, "plain_forward_ms": 1e3 * t_plain,
                      "gradient_over_forward": (t_fwd + t_bwd) / t_plain}
+        if prec == "fp64":
+            res[prec]["fd_nonsmooth_point"] = fd_at_literal_state(s, q, gq, dts, rho_target, n)
+        s.close()
         del q, UT, lam, gq
         torch.cuda.empty_cache()
     return res
@@ -465,6 +590,17 @@ def run_ours(args, dist):
                               / 1e9) / peak}
 
     out = {}
+    alu = None
+    if not args.no_peaks and dist.rank == 0:
+        alu = alu_peaks(dist.local_rank)
+        out["alu_peaks"] = alu
+        alg = algorithmic_flops()
+        if alg is not None:  # the FP32 step's arithmetic against the paired-FP32 peak (context: it is HBM-bound)
+            roofline["alu_context"] = {
+                "flops_per_cell_step": alg["step"],
+                "achieved": alg["step"] * cells * args.steps / t_local / 1e12, "unit": "TFLOP/s",
+                "peak": alu["fp32_paired"],
+                "frac": alg["step"] * cells * args.steps / t_local / 1e12 / alu["fp32_paired"]}
     # FP64 path on the same workload, and the FP32-vs-FP64 error after those steps
     if prec == "fp32" and not args.no_fp64 and dist.rank == 0:
         s64 = LagrangeFlux(Config(precision="fp64", **kw))
@@ -504,7 +640,7 @@ def run_ours(args, dist):
         del ref, got
         v64 = cells * args.fp64_steps / t64
         out["fp64"] = {"value": v64, "unit": METRIC, "steps": args.fp64_steps, "ms_per_step": 1e3 * t64 / args.fp64_steps,
-                       "stage_ms": [m0, m1], "roofline": fp64_alu_roofline([m0, m1], cells)}
+                       "stage_ms": [m0, m1], "roofline": fp64_alu_roofline([m0, m1], cells, alu)}
         out["fp32_over_fp64"] = value / dist.world / v64
         out["l1_error"] = {"fp32_vs_fp64_relative_l1": dict(zip(["rho", "rhou", "rhov", "rhoE"], l1)),
                            "after_steps": args.fp64_steps}

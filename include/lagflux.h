@@ -229,6 +229,14 @@ lf_status lf_profile_read(lf_ctx* ctx, double ms[2], int64_t launches[2]);
  * differentiated piecewise; at non-smooth points max/min take the first
  * argument on ties, the limiter has zero derivative where ab <= 0, and the
  * upwind side follows the sign of u*.
+ *
+ * The paper states the step (Sec. 4, steps 1-11) but no adjoint; the calls
+ * below differentiate exactly that step.  The adjoint needs dJ/dU(T), which
+ * for most objectives depends on U(T), so the work is split in two calls:
+ * lf_adjoint_forward (run and record) and lf_adjoint_backward (sweep back
+ * from a given dJ/dU(T)).  lf_adjoint runs both in one call for objectives
+ * whose dJ/dU(T) is known before the run (linear functionals of U(T), or a
+ * cotangent computed from an earlier run of the same state).
  * ------------------------------------------------------------------------ */
 
 /* Runs nsteps CFL steps from the context's current state (as lf_step does),
@@ -236,17 +244,36 @@ lf_status lf_profile_read(lf_ctx* ctx, double ms[2], int64_t launches[2]);
  * dt of every step; the context ends at the final state U(T).  Allocates the
  * checkpoints (ceil(nsteps / ceil(sqrt(nsteps))) states), one segment of
  * recomputed states and adjoint work buffers; they are kept for reuse until
- * lf_destroy.  dts_out (nullable, nsteps doubles) receives the dt sequence.
- * Synchronises. */
+ * lf_destroy.  dts_out (nullable, host, nsteps doubles) receives the dt
+ * sequence.  Synchronises. */
 lf_status lf_adjoint_forward(lf_ctx* ctx, int32_t nsteps, double* dts_out);
 
-/* Given lambda_T = dJ/dU(T) (device, 4 dense planes of the configured
- * precision, conservative variables, x fastest), computes dJ/dU(0) of the
- * last recorded forward run by sweeping its checkpoints backwards.
- * grad_U0 (nullable): device, 4 dense planes of dJ/dU(0).
- * grad_q0 (nullable): device, 4 dense planes of dJ/d(rho, u, v, p) at t = 0.
+/* Given lambda_T = dJ/dU(T) (4 dense planes of the configured precision,
+ * conservative variables, x fastest), computes dJ/dU(0) of the last recorded
+ * forward run by sweeping its checkpoints backwards.
+ * grad_U0 (nullable): 4 dense planes of dJ/dU(0).
+ * grad_q0 (nullable): 4 dense planes of dJ/d(rho, u, v, p) at t = 0.
+ * on_device: 1 = the three buffers are device pointers, 0 = host pointers.
  * The context's state (U(T)) is left unchanged.  Synchronises. */
-lf_status lf_adjoint_backward(lf_ctx* ctx, const void* lambda_T, void* grad_U0, void* grad_q0);
+lf_status lf_adjoint_backward(lf_ctx* ctx, const void* lambda_T, void* grad_U0, void* grad_q0, int on_device);
+
+/* lf_adjoint_forward(ctx, nsteps, dts_out) followed by
+ * lf_adjoint_backward(ctx, lambda_T, grad_U0, grad_q0, on_device): the
+ * gradient of an objective with the given dJ/dU(T) with respect to the
+ * context's current state.  The context ends at U(T).  Synchronises. */
+lf_status lf_adjoint(lf_ctx* ctx, int32_t nsteps, const void* lambda_T, void* grad_U0, void* grad_q0,
+                     double* dts_out, int on_device);
+
+/* How the reverse sweep forms the forward quantities it differentiates (the
+ * primitives, limited slopes and limiter derivatives of a state).
+ * LF_ADJOINT_PASSES_TABLES: one prep pass per state writes them to tables
+ * (28 values per cell) that the face and cell passes read;
+ * LF_ADJOINT_PASSES_DIRECT: every face and cell thread recomputes them from
+ * the state.  The two give the same derivative up to rounding order.
+ * LF_ADJOINT_PASSES_AUTO (default): tables in FP64 (divisions dominate
+ * there), direct in FP32 (the extra passes and table traffic dominate). */
+enum { LF_ADJOINT_PASSES_AUTO = 0, LF_ADJOINT_PASSES_TABLES = 1, LF_ADJOINT_PASSES_DIRECT = 2 };
+lf_status lf_adjoint_set_passes(lf_ctx* ctx, int32_t passes);
 
 /* ------------------------------------------------------------------------
  * Batched mode: many independent 2D meshes of uneven sizes advanced together
@@ -319,14 +346,40 @@ const char* lf_batch_last_error(const lf_batch* b);
  *            non-positive density or pressure.  If NULL the call only
  *            enqueues and reports no device-side error.
  *   stream : cudaStream_t (NULL: default stream) on device cfg->device.
- * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  All calls share
+ * On LF_ERR_NONPHYSICAL, and whenever dt_used is NULL and U_in is not a
+ * valid state, U_out is unspecified: a non-physical input or a bad CFL dt
+ * stops the step before the update, so U_out may keep what it held before
+ * the call.  Only LF_OK with dt_used given certifies U_out.
+ * The first successful call on a device looks up the array's device address
+ * (once per device; a failed lookup is retried by the next call); make that
+ * first call before any stream capture: a first call on a capturing stream
+ * returns LF_ERR_ARG.  All calls share
  * the array: calls whose GPU work overlaps (e.g. on two streams) race.
  * Error text: lf_last_error(NULL). */
 #define LF_NOALLOC_MAX_CELLS (1LL << 18)
 #define LF_NOALLOC_SCRATCH_BYTES (256 + 4 * 8 * LF_NOALLOC_MAX_CELLS)
 lf_status lf_step_noalloc(const lf_config* cfg, const void* U_in, void* U_out, double dt, double* dt_used,
                           void* stream);
+
+/* ------------------------------------------------------------------------
+ * Measurement helper (the paper has no counterpart: its roofline analysis is
+ * for multicore CPUs).  Measures the arithmetic peak that the ALU rooflines
+ * of the stage kernels are taken against: eight independent fused
+ * multiply-add chains per thread over 8 CTAs of 256 threads per SM, the
+ * iteration count calibrated to about target_ms per launch, best of three
+ * timed launches (CUDA events) after two calibration launches.
+ *   device   : CUDA device ordinal (made current for the call, then restored).
+ *   kind     : LF_PEAK_FP64 (DFMA), LF_PEAK_FP32 (FFMA) or
+ *              LF_PEAK_FP32_PAIRED (the paired FP32 FMA the FP32 stage
+ *              kernels use: two lanes per instruction).
+ *   target_ms: in (0, 1000].
+ *   tflops   : receives the measured rate, counting a fused multiply-add as
+ *              two flops.
+ * Allocates and frees a small result buffer, a stream and two events;
+ * synchronises.  The SM clock is whatever the GPU runs at: sample it beside
+ * the call to compare with a nominal rate. */
+enum { LF_PEAK_FP64 = 0, LF_PEAK_FP32 = 1, LF_PEAK_FP32_PAIRED = 2 };
+lf_status lf_measure_peak(int32_t device, int32_t kind, double target_ms, double* tflops);
 
 /* Human-readable name of a status code (static storage). */
 const char* lf_status_string(lf_status s);

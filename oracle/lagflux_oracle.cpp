@@ -14,8 +14,14 @@
 // every face flux stored before any cell is updated.  Compiled with
 // -ffp-contract=off so that no fused multiply-add changes the rounding.
 //
-// Readings of points where the paper is silent (each is repeated in the
-// design notes):
+// The `#pragma omp` lines act only in a second build of this same file with
+// -fopenmp, used to time the oracle on all host cores beside the GPU.  Every
+// loop they split writes each element from one iteration, and the only
+// reductions are a logical AND and an exact maximum, so that build returns
+// the same bits as the plain single-threaded one.
+//
+// Readings of points where the paper is silent (the CUDA library takes the
+// same readings):
 //   * CFL condition (Sec. 4, Heun step 1 requires a CFL condition without
 //     writing it out): dt = CFL / max_K sum_d (|u_d,K| + c_K) / dx_d over the
 //     mesh's axes (1D: x; 2D: x, y; 3D: x, y, z), from U^n, the same dt for
@@ -46,6 +52,9 @@
 #include <cstdint>
 #include <cstring>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -76,6 +85,27 @@ inline double val(double x) { return x; }
 inline double val(const Dual& x) { return x.v; }
 inline double sq_root(double x) { return std::sqrt(x); }
 inline Dual sq_root(const Dual& x) { return sqrt(x); }
+
+// Op-counting scalar: a double that tallies each arithmetic operation it
+// takes part in (add or subtract, multiply, divide, square root), used only to
+// count the method's flops per cell (oracle_count_ops), never to step.
+// Negation, absolute values, comparisons and sign tests are not counted.
+struct OpTally {
+  double add = 0, mul = 0, div = 0, sqrt = 0;
+};
+OpTally g_tally;
+struct Counted {
+  double v;
+  Counted() : v(0) {}
+  Counted(double x) : v(x) {}
+};
+inline Counted operator+(Counted a, Counted b) { g_tally.add += 1; return Counted(a.v + b.v); }
+inline Counted operator-(Counted a, Counted b) { g_tally.add += 1; return Counted(a.v - b.v); }
+inline Counted operator-(Counted a) { return Counted(-a.v); }
+inline Counted operator*(Counted a, Counted b) { g_tally.mul += 1; return Counted(a.v * b.v); }
+inline Counted operator/(Counted a, Counted b) { g_tally.div += 1; return Counted(a.v / b.v); }
+inline double val(const Counted& x) { return x.v; }
+inline Counted sq_root(const Counted& x) { g_tally.sqrt += 1; return Counted(std::sqrt(x.v)); }
 
 template <class S> inline S abs_s(const S& a) { return val(a) < 0.0 ? S(-a) : a; }
 // First argument on ties.
@@ -291,6 +321,7 @@ bool build_primitives(const Mesh<S>& m, const std::vector<S> U[], std::vector<S>
   const int nf = nfields(c);
   for (int l = 0; l < nf; ++l) qg[l].assign((size_t)m.ext[0] * m.ext[1] * m.ext[2], S(0.0));
   bool physical = true;
+#pragma omp parallel for collapse(2) reduction(&& : physical)
   for (int k = -m.g[2]; k < m.n[2] + m.g[2]; ++k)
     for (int j = -m.g[1]; j < m.n[1] + m.g[1]; ++j)
       for (int i = -m.g[0]; i < m.n[0] + m.g[0]; ++i) {
@@ -324,6 +355,7 @@ bool all_face_fluxes(const Mesh<S>& m, const std::vector<S> U[], std::vector<S> 
     for (int l = 0; l < nf; ++l) F[d][l].assign(m.nfaces(d), S(0.0));
     int e[3] = {m.n[0], m.n[1], m.n[2]};
     e[d] += 1;
+#pragma omp parallel for collapse(2)
     for (int k = 0; k < e[2]; ++k)
       for (int j = 0; j < e[1]; ++j)
         for (int i = 0; i < e[0]; ++i) {
@@ -362,17 +394,26 @@ S flux_balance(const Mesh<S>& m, const std::vector<S> F[3][MAXF], int l, int i, 
   return acc / K;
 }
 
+// The CFL reading stated at the top of this file: sum over the mesh's axes
+// of (|u_d| + c) / dx_d for one cell's primitive state q.
+template <class S>
+S wave_speed_sum(const OracleConfig& c, const double h[3], const S q[]) {
+  S a = sound_speed(c, q[0], q[ien(c)]);
+  S s = S(0.0);
+  for (int d = 0; d < c.dim; ++d) s = s + (abs_s(q[1 + d]) + a) / h[d];
+  return s;
+}
+
 // Heun step 1 under the CFL reading stated at the top of this file.
 double cfl_dt(const OracleConfig& c, const std::vector<double> U[]) {
   Mesh<double> m(c);
   double smax = 0.0;
+#pragma omp parallel for reduction(max : smax)
   for (size_t k = 0; k < m.ncell(); ++k) {
     double Uc[MAXF], q[MAXF];
     for (int l = 0; l < nfields(c); ++l) Uc[l] = U[l][k];
     prim_from_cons(c, Uc, q);
-    double a = sound_speed(c, q[0], q[ien(c)]);
-    double s = 0.0;
-    for (int d = 0; d < c.dim; ++d) s += (std::fabs(q[1 + d]) + a) / m.h[d];
+    double s = wave_speed_sum(c, m.h, q);
     if (s > smax) smax = s;
   }
   return c.cfl / smax;
@@ -383,6 +424,7 @@ template <class S>
 bool state_physical(const Mesh<S>& m, const std::vector<S> U[]) {
   const OracleConfig& c = m.c;
   bool ok = true;
+#pragma omp parallel for reduction(&& : ok)
   for (size_t k = 0; k < m.ncell(); ++k) {
     S Uc[MAXF], q[MAXF];
     for (int l = 0; l < nfields(c); ++l) Uc[l] = U[l][k];
@@ -400,6 +442,7 @@ bool heun_step(const OracleConfig& c, std::vector<S> U[], double dt) {
   std::vector<S> Fn[3][MAXF], Fs[3][MAXF], Us[MAXF];
   bool ok = all_face_fluxes(m, U, Fn);  // steps 2-5
   for (int l = 0; l < nf; ++l) Us[l].resize(m.ncell());
+#pragma omp parallel for collapse(2)
   for (int k = 0; k < m.n[2]; ++k)  // step 6: predicted states
     for (int j = 0; j < m.n[1]; ++j)
       for (int i = 0; i < m.n[0]; ++i) {
@@ -407,6 +450,7 @@ bool heun_step(const OracleConfig& c, std::vector<S> U[], double dt) {
         for (int l = 0; l < nf; ++l) Us[l][x] = U[l][x] - dt * flux_balance(m, Fn, l, i, j, k);
       }
   ok = all_face_fluxes(m, Us, Fs) && ok;  // steps 7-10
+#pragma omp parallel for collapse(2)
   for (int k = 0; k < m.n[2]; ++k)  // step 11: averaged fluxes
     for (int j = 0; j < m.n[1]; ++j)
       for (int i = 0; i < m.n[0]; ++i) {
@@ -472,6 +516,98 @@ void load_planes(const OracleConfig& c, const double* src, std::vector<double> U
 void store_planes(const OracleConfig& c, const std::vector<double> U[], double* dst) {
   size_t n = (size_t)c.nx * c.ny * c.nz;
   for (int l = 0; l < nfields(c); ++l) std::memcpy(dst + l * n, U[l].data(), n * sizeof(double));
+}
+
+// Flops of one stage of the method on state U, in the minimal schedule: each
+// cell's primitive state, each cell's limited slope per axis and field, each
+// face's states and Lagrange flux, and each cell's flux balance formed once
+// (the step above stores both face states' slopes and re-forms the flux
+// balance of U^n in step 11; those repeats are the oracle's literal form, not
+// work the method needs).  Faces wrap around on every axis, so a row of n
+// cells has n faces.  tally[s] receives the operations of part s, summed over
+// all cells: 0 primitives, 1 slopes, 2 face states and fluxes, 3 flux
+// balances, 4 the predictor update U - dt b, 5 the corrector update
+// U - dt (b_n + b_*)/2 (whose b_n the predictor already formed), 6 the
+// wave-speed sum of the CFL condition.
+constexpr int kCountParts = 7;
+void count_stage_ops(const OracleConfig& c, const std::vector<double> U[], OpTally tally[kCountParts]) {
+  Mesh<Counted> m(c);
+  const int nf = nfields(c);
+  const size_t n = m.ncell();
+  auto wrapped = [&](int i, int j, int k, int d, int s) {  // cell s steps along axis d, periodic
+    int o[3] = {i, j, k};
+    o[d] = wrap_index(o[d] + s, m.n[d], BC_PERIODIC);
+    return m.cell(o[0], o[1], o[2]);
+  };
+  std::vector<Counted> q[MAXF], sig[3][MAXF], F[3][MAXF];
+  for (int l = 0; l < nf; ++l) q[l].resize(n);
+  g_tally = OpTally();
+  for (size_t x = 0; x < n; ++x) {  // 0: primitives
+    Counted Uc[MAXF], qc[MAXF];
+    for (int l = 0; l < nf; ++l) Uc[l] = Counted(U[l][x]);
+    prim_from_cons(c, Uc, qc);
+    for (int l = 0; l < nf; ++l) q[l][x] = qc[l];
+  }
+  tally[0] = g_tally;
+  g_tally = OpTally();
+  for (int d = 0; d < c.dim; ++d)  // 1: limited slopes
+    for (int l = 0; l < nf; ++l) {
+      sig[d][l].resize(n);
+      for (int k = 0; k < m.n[2]; ++k)
+        for (int j = 0; j < m.n[1]; ++j)
+          for (int i = 0; i < m.n[0]; ++i) {
+            size_t x = m.cell(i, j, k);
+            sig[d][l][x] = limiter(c, q[l][x] - q[l][wrapped(i, j, k, d, -1)], q[l][wrapped(i, j, k, d, 1)] - q[l][x]);
+          }
+    }
+  tally[1] = g_tally;
+  g_tally = OpTally();
+  for (int d = 0; d < c.dim; ++d) {  // 2: face states and fluxes (face behind each cell)
+    for (int l = 0; l < nf; ++l) F[d][l].resize(m.nfaces(d));
+    for (int k = 0; k < m.n[2]; ++k)
+      for (int j = 0; j < m.n[1]; ++j)
+        for (int i = 0; i < m.n[0]; ++i) {
+          size_t xr = m.cell(i, j, k), xl = wrapped(i, j, k, d, -1);
+          Counted qL[MAXF], qR[MAXF], Fv[MAXF];
+          for (int l = 0; l < nf; ++l) {
+            qL[l] = q[l][xl] + 0.5 * sig[d][l][xl];
+            qR[l] = q[l][xr] - 0.5 * sig[d][l][xr];
+          }
+          face_flux(c, d, qL, qR, Fv);
+          int hi[3] = {i, j, k};
+          for (int l = 0; l < nf; ++l) F[d][l][m.fidx(d, i, j, k)] = Fv[l];
+          if (hi[d] == 0) {  // the same face closes the far end of the row
+            hi[d] = m.n[d];
+            for (int l = 0; l < nf; ++l) F[d][l][m.fidx(d, hi[0], hi[1], hi[2])] = Fv[l];
+          }
+        }
+  }
+  tally[2] = g_tally;
+  std::vector<Counted> b[MAXF];
+  g_tally = OpTally();
+  for (int l = 0; l < nf; ++l) {  // 3: flux balances
+    b[l].resize(n);
+    for (int k = 0; k < m.n[2]; ++k)
+      for (int j = 0; j < m.n[1]; ++j)
+        for (int i = 0; i < m.n[0]; ++i) b[l][m.cell(i, j, k)] = flux_balance(m, F, l, i, j, k);
+  }
+  tally[3] = g_tally;
+  const Counted dt(1e-3);
+  g_tally = OpTally();
+  for (int l = 0; l < nf; ++l)  // 4: predictor update
+    for (size_t x = 0; x < n; ++x) (void)(Counted(U[l][x]) - dt * b[l][x]);
+  tally[4] = g_tally;
+  g_tally = OpTally();
+  for (int l = 0; l < nf; ++l)  // 5: corrector update (b stands for both b_n and b_*)
+    for (size_t x = 0; x < n; ++x) (void)(Counted(U[l][x]) - dt * ((b[l][x] + b[l][x]) / 2.0));
+  tally[5] = g_tally;
+  g_tally = OpTally();
+  for (size_t x = 0; x < n; ++x) {  // 6: wave-speed sum
+    Counted qc[MAXF];
+    for (int l = 0; l < nf; ++l) qc[l] = q[l][x];
+    (void)wave_speed_sum(c, m.h, qc);
+  }
+  tally[6] = g_tally;
 }
 
 }  // namespace
@@ -618,6 +754,45 @@ int oracle_run_tangent(const OracleConfig* c, const double* q0, const double* dq
       dU_out[l * n + k] = U[l][k].d;
     }
   return status;
+}
+
+// Flops per cell of the method on the state U (count_stage_ops): out[4 s + k]
+// for part s = 0 .. 6 and k = add, multiply, divide, square root, each summed
+// over the mesh and divided by the number of cells.  Counting is serial: the
+// OpenMP build refuses it (ORC_ARG).
+int oracle_count_ops(const OracleConfig* c, const double* U_in, double* out) {
+#ifdef _OPENMP
+  (void)c;
+  (void)U_in;
+  (void)out;
+  return ORC_ARG;
+#else
+  if (!config_ok(c) || !U_in || !out) return ORC_ARG;
+  std::vector<double> U[MAXF];
+  load_planes(*c, U_in, U);
+  OpTally t[kCountParts];
+  count_stage_ops(*c, U, t);
+  const double n = (double)c->nx * c->ny * c->nz;
+  for (int s = 0; s < kCountParts; ++s) {
+    out[4 * s + 0] = t[s].add / n;
+    out[4 * s + 1] = t[s].mul / n;
+    out[4 * s + 2] = t[s].div / n;
+    out[4 * s + 3] = t[s].sqrt / n;
+  }
+  return ORC_OK;
+#endif
+}
+
+// Threads of the OpenMP timing build: sets the count when n > 0 and returns
+// the count the next parallel loop will use (always 1 in the plain build).
+int oracle_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 }  // extern "C"

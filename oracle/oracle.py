@@ -118,6 +118,28 @@ def build(force: bool = False) -> str:
         return _LIB
 
 
+_LIB_OMP = os.path.join(_HERE, "liblagflux_oracle_omp.so")
+
+
+def build_omp(force: bool = False) -> str:
+    """The same source compiled with -fopenmp: the timing build that runs the
+    oracle's cell and face loops on all host cores (same bits as build())."""
+    with _lock:
+        if not force and os.path.exists(_LIB_OMP) and os.path.getmtime(_LIB_OMP) >= os.path.getmtime(_SRC):
+            return _LIB_OMP
+        tmp = _LIB_OMP + f".tmp{os.getpid()}"
+        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC",
+               "-o", tmp, _SRC]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_OMP)
+        return _LIB_OMP
+
+
+def threads(n: int = 0) -> int:
+    """Sets (n > 0) and returns the thread count of the loaded oracle build."""
+    return int(_load().oracle_threads(int(n)))
+
+
 def _declare(lib):
     P = ctypes.POINTER
     d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
@@ -131,6 +153,8 @@ def _declare(lib):
     lib.oracle_residual.argtypes = [P(_Cfg), pd, pd]
     lib.oracle_run.argtypes = [P(_Cfg), pd, i32, d, d, pd, pd, P(i32), pd]
     lib.oracle_run_tangent.argtypes = [P(_Cfg), pd, pd, i32, pd, pd, pd]
+    lib.oracle_threads.argtypes = [ctypes.c_int]
+    lib.oracle_count_ops.argtypes = [P(_Cfg), pd, pd]
     return lib
 
 
@@ -311,3 +335,33 @@ def run_tangent(cfg: OracleConfig, q0, dq0, dts):
     _check(_load().oracle_run_tangent(ctypes.byref(c), _ptr(q0), _ptr(dq0), len(dts), _ptr(dts),
                                       _ptr(U), _ptr(dU)))
     return U, dU
+
+
+COUNT_PARTS = ("primitives", "slopes", "faces", "balances", "predictor_update", "corrector_update", "wave_speed")
+COUNT_KINDS = ("add", "mul", "div", "sqrt")
+
+
+def count_ops(cfg: OracleConfig, U) -> dict:
+    """Operations per cell of the method on state U, part by part (minimal
+    schedule: every primitive state, slope, face flux and flux balance formed
+    once; see count_stage_ops in the C++ source): {part: {kind: count}}."""
+    U = _state(cfg, U)
+    out = np.zeros(4 * len(COUNT_PARTS))
+    c = cfg.to_c()
+    _check(_load().oracle_count_ops(ctypes.byref(c), _ptr(U), _ptr(out)))
+    return {p: dict(zip(COUNT_KINDS, out[4 * i:4 * i + 4].tolist())) for i, p in enumerate(COUNT_PARTS)}
+
+
+def flops_per_cell(counts: dict) -> dict:
+    """Flops per cell of the predictor, the corrector (with the CFL wave-speed
+    sum of the next step) and the whole Heun step, each operation counted as
+    one flop; `div_sqrt` is how many of them are divisions or square roots."""
+    tot = {p: sum(v.values()) for p, v in counts.items()}
+    ds = {p: v["div"] + v["sqrt"] for p, v in counts.items()}
+    stage = ("primitives", "slopes", "faces", "balances")
+    pred = sum(tot[p] for p in stage) + tot["predictor_update"]
+    corr = sum(tot[p] for p in stage) + tot["corrector_update"] + tot["wave_speed"]
+    pred_ds = sum(ds[p] for p in stage) + ds["predictor_update"]
+    corr_ds = sum(ds[p] for p in stage) + ds["corrector_update"] + ds["wave_speed"]
+    return {"predictor": pred, "corrector": corr, "step": pred + corr,
+            "div_sqrt": {"predictor": pred_ds, "corrector": corr_ds, "step": pred_ds + corr_ds}}

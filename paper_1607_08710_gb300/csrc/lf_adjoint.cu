@@ -42,6 +42,12 @@ const char* adjoint_unsupported(const lf_ctx* c) {
   return nullptr;
 }
 
+bool uses_tables(const lf_ctx* c) {
+  if (c->adj_passes == LF_ADJOINT_PASSES_TABLES) return true;
+  if (c->adj_passes == LF_ADJOINT_PASSES_DIRECT) return false;
+  return c->elem == 8;
+}
+
 template <typename T>
 lf_status backward_t(lf_ctx* c) {
   auto& A = c->adj;
@@ -51,10 +57,15 @@ lf_status backward_t(lf_ctx* c) {
   T* lamstar = static_cast<T*>(A.lamstar);
   T* fx = static_cast<T*>(A.fx);
   T* fy = static_cast<T*>(A.fy);
-  constexpr bool kTables = sizeof(T) == 8;
-  T* Q = static_cast<T*>(A.prep);  // FP64 only
-  T* tabx = kTables ? Q + 4 * (size_t)m.nx * m.ny : nullptr;
-  T* taby = kTables ? tabx + 12 * (size_t)(m.nx + 2) * m.ny : nullptr;
+  const bool tables = uses_tables(c);
+  if (tables) {
+    const size_t prep_elems =
+        4 * (size_t)m.nx * m.ny + 12 * ((size_t)(m.nx + 2) * m.ny + (size_t)(m.ny + 2) * m.nx);
+    if (lf_status st = grow(c, &A.prep, &A.prep_cap, prep_elems * c->elem)) return st;
+  }
+  T* Q = static_cast<T*>(A.prep);
+  T* tabx = tables ? Q + 4 * (size_t)m.nx * m.ny : nullptr;
+  T* taby = tables ? tabx + 12 * (size_t)(m.nx + 2) * m.ny : nullptr;
   T* Us = static_cast<T*>(c->Ustar);
   LF_CUDA(c, lf::launch_reset_scalars(A.sc, c->cfg.cfl, s));
   const int nseg = (A.nsteps + A.seg - 1) / A.seg;
@@ -79,10 +90,11 @@ lf_status backward_t(lf_ctx* c) {
       LF_CUDA(c, lf::launch_stage<T>(0, m, Un, Un, Us, A.sc, s));
       LF_CUDA(c, lf::launch_end_step(A.sc, s));
       // lambda* = lambda/2 - dt/2 (dD/dU)(U*)^T lambda, then
-      // lambda <- lambda/2 + lambda* - dt (dD/dU)(U^n)^T lambda*.  FP64 reads
-      // the forward quantities from prep tables (its divisions dominate);
-      // FP32 recomputes them in the two passes (measured faster there).
-      if (kTables) {
+      // lambda <- lambda/2 + lambda* - dt (dD/dU)(U^n)^T lambda*.  The table
+      // passes read the forward quantities from prep tables (FP64 default:
+      // its divisions dominate); the direct passes recompute them (FP32
+      // default: measured faster there).
+      if (tables) {
         LF_CUDA(c, lf::launch_adjoint_prep<T>(m, Us, Q, tabx, taby, s));
         LF_CUDA(c, lf::launch_face_vjp<T>(m, 0, Q, tabx, lam, fx, s));
         LF_CUDA(c, lf::launch_face_vjp<T>(m, 1, Q, taby, lam, fy, s));
@@ -156,11 +168,6 @@ lf_status lf_adjoint_forward(lf_ctx* c, int32_t nsteps, double* dts_out) {
   if (lf_status st = grow(c, &A.fx, &fx_cap, faces * 8 * c->elem)) return st;
   if (lf_status st = grow(c, &A.fy, &fy_cap, faces * 8 * c->elem)) return st;
   A.face_cap = fx_cap < fy_cap ? fx_cap : fy_cap;
-  if (c->elem == 8) {  // FP64 reverse sweeps read prep tables
-    const size_t prep_elems =
-        4 * (size_t)m.nx * m.ny + 12 * ((size_t)(m.nx + 2) * m.ny + (size_t)(m.ny + 2) * m.nx);
-    if (lf_status st = grow(c, &A.prep, &A.prep_cap, prep_elems * c->elem)) return st;
-  }
   if (lf_status st = grow(c, reinterpret_cast<void**>(&A.dts_dev), &A.dts_cap, nsteps * sizeof(double))) return st;
   if (lf_status st = grow(c, reinterpret_cast<void**>(&A.sc), &sc_cap, sizeof(lf::Scalars))) return st;
   for (int n = 0; n < nsteps; ++n) {
@@ -184,7 +191,7 @@ lf_status lf_adjoint_forward(lf_ctx* c, int32_t nsteps, double* dts_out) {
   return LF_OK;
 }
 
-lf_status lf_adjoint_backward(lf_ctx* c, const void* lambda_T, void* grad_U0, void* grad_q0) {
+lf_status lf_adjoint_backward(lf_ctx* c, const void* lambda_T, void* grad_U0, void* grad_q0, int on_device) {
   if (!c) return LF_ERR_ARG;
   if (!lambda_T) {
     set_err(c, "lf_adjoint_backward: lambda_T is NULL");
@@ -199,26 +206,52 @@ lf_status lf_adjoint_backward(lf_ctx* c, const void* lambda_T, void* grad_U0, vo
   const lf::MeshDesc& m = c->mesh;
   const size_t w = (size_t)m.nx * c->elem, dp = (size_t)m.pitch * c->elem;
   const size_t dense_plane = (size_t)m.nx * m.ny * c->elem;
+  const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   for (int l = 0; l < 4; ++l)
     LF_CUDA(c, cudaMemcpy2DAsync(static_cast<char*>(A.lam) + (size_t)l * m.plane * c->elem, dp,
-                                 static_cast<const char*>(lambda_T) + l * dense_plane, w, w, m.ny,
-                                 cudaMemcpyDeviceToDevice, c->stream));
+                                 static_cast<const char*>(lambda_T) + l * dense_plane, w, w, m.ny, kin, c->stream));
   lf_status st = c->elem == 8 ? backward_t<double>(c) : backward_t<float>(c);
   if (st != LF_OK) return st;
   if (grad_U0)
     for (int l = 0; l < 4; ++l)
       LF_CUDA(c, cudaMemcpy2DAsync(static_cast<char*>(grad_U0) + l * dense_plane, w,
                                    static_cast<const char*>(A.lam) + (size_t)l * m.plane * c->elem, dp, w, m.ny,
-                                   cudaMemcpyDeviceToDevice, c->stream));
+                                   kout, c->stream));
   if (grad_q0) {
+    // host output: the dense planes are formed in the x-face buffer (at least
+    // 8 (nx+1) ny values, more than the 4 nx ny needed) and copied out
+    void* gq = on_device ? grad_q0 : A.fx;
     cudaError_t e = c->elem == 8
         ? lf::launch_grad_prim<double>(m, static_cast<const double*>(A.ck), static_cast<const double*>(A.lam),
-                                       static_cast<double*>(grad_q0), c->stream)
+                                       static_cast<double*>(gq), c->stream)
         : lf::launch_grad_prim<float>(m, static_cast<const float*>(A.ck), static_cast<const float*>(A.lam),
-                                      static_cast<float*>(grad_q0), c->stream);
+                                      static_cast<float*>(gq), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "grad_prim launch");
+    if (!on_device) LF_CUDA(c, cudaMemcpyAsync(grad_q0, gq, 4 * dense_plane, kout, c->stream));
   }
   LF_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LF_OK;
+}
+
+lf_status lf_adjoint(lf_ctx* c, int32_t nsteps, const void* lambda_T, void* grad_U0, void* grad_q0, double* dts_out,
+                     int on_device) {
+  if (!c) return LF_ERR_ARG;
+  if (!lambda_T) {
+    set_err(c, "lf_adjoint: lambda_T is NULL");
+    return LF_ERR_ARG;
+  }
+  if (lf_status st = lf_adjoint_forward(c, nsteps, dts_out)) return st;
+  return lf_adjoint_backward(c, lambda_T, grad_U0, grad_q0, on_device);
+}
+
+lf_status lf_adjoint_set_passes(lf_ctx* c, int32_t passes) {
+  if (!c) return LF_ERR_ARG;
+  if (passes != LF_ADJOINT_PASSES_AUTO && passes != LF_ADJOINT_PASSES_TABLES && passes != LF_ADJOINT_PASSES_DIRECT) {
+    set_err(c, "lf_adjoint_set_passes: passes must be LF_ADJOINT_PASSES_AUTO, _TABLES or _DIRECT (got %d)", passes);
+    return LF_ERR_ARG;
+  }
+  c->adj_passes = passes;
   return LF_OK;
 }
 

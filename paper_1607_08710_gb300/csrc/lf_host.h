@@ -54,6 +54,7 @@ struct lf_ctx {
     double* dts_dev = nullptr; // dt of each forward step, recorded on the device
     lf::Scalars* sc = nullptr; // scalars of the recomputation
   } adj;
+  int adj_passes = LF_ADJOINT_PASSES_AUTO;  // lf_adjoint_set_passes
   char last_error[512] = {0};
 };
 

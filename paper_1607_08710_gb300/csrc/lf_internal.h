@@ -36,8 +36,8 @@ struct MeshDesc {
   int riemann;       // RIEMANN_*
   double gamma, beta;
   double rdx, rdy;   // 1 / dx, 1 / dy
-  int vec;           // 1: pitch and plane even and every state buffer 16-byte
-                     // aligned, so two adjacent cells may be moved as one vector
+  int vec;           // 1: pitch and plane even and every state buffer aligned to
+                     // 8 bytes, so two adjacent FP32 cells may be moved as one vector
   int nspecies = 0;  // transported mass fractions: planes 4 .. 3 + nspecies hold rho y_k
   int ty = 0;        // rows per tile of the 2D stage kernels (0: the compiled default)
 };

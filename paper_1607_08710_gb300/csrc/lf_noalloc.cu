@@ -15,8 +15,11 @@
 // Host code cannot use the array's name as a device address (on the host it
 // is only a stand-in symbol), so the first call on each device looks up the
 // real address with cudaGetSymbolAddress, with that device current, checks
-// the result and caches it; later calls reuse it.  Because that lookup may
-// load the module, make the first call on a device before any stream capture.
+// the result and caches it; later calls reuse it.  A failed lookup is not
+// cached: the next call tries again.  Because the lookup may load the module,
+// the first call on a device must come before any stream capture; a first
+// call made on a stream that is being captured is refused (LF_ERR_ARG) before
+// it touches the device.
 //
 // Every call shares the one array and the array keeps the previous call's
 // contents: each call clears the scalars it needs (dt, wave-speed maximum,
@@ -30,6 +33,7 @@
 
 #include "../../include/lagflux.h"
 #include "lf_internal.h"
+#include "lf_stage.cuh"
 
 namespace {
 
@@ -44,20 +48,49 @@ static_assert(kScratchBytes == LF_NOALLOC_SCRATCH_BYTES, "header and library dis
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-std::once_flag g_once[kMaxDevices];
-cudaError_t g_setup_status[kMaxDevices];
+std::mutex g_lookup_mutex;
+bool g_found[kMaxDevices];
 void* g_scratch_addr[kMaxDevices];
 
-// Once per device, with that device current: the device address of g_scratch.
-cudaError_t scratch_address(int dev, void** out) {
-  std::call_once(g_once[dev], [dev] {
+// The device address of g_scratch on `dev` (the current device), looked up
+// on the first successful call for that device and cached.
+lf_status scratch_address(int dev, cudaStream_t s, void** out) {
+  std::lock_guard<std::mutex> lock(g_lookup_mutex);
+  if (!g_found[dev]) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+      cudaGetLastError();  // leave no pending error for the caller's next launch check
+      lf::set_init_error("lf_step_noalloc: the first call on device %d looks up the scratch address and must not "
+                         "be made while its stream is being captured (%s)",
+                         dev, e != cudaSuccess ? cudaGetErrorString(e) : "stream is capturing");
+      return LF_ERR_ARG;
+    }
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    g_setup_status[dev] = e;
-    g_scratch_addr[dev] = e == cudaSuccess ? p : nullptr;
-  });
+    e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      lf::set_init_error("lf_step_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      return LF_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = p;
+    g_found[dev] = true;
+  }
   *out = g_scratch_addr[dev];
-  return g_setup_status[dev];
+  return LF_OK;
+}
+
+// The FP32 stage kernels move CPL consecutive cells of a lane with one vector
+// copy (CPL * sizeof(T) bytes) when the mesh description allows it (m.vec);
+// FP64 kernels (CPL = 1) copy single cells.  Vector copies start at even
+// columns of every row of every plane, so dense planes need nx to be a
+// multiple of CPL and both state buffers aligned to the vector width.
+template <typename T>
+bool vector_access_ok(int nx, const void* a, const void* b) {
+  constexpr int cpl = lf::StageShape<T>::CPL;
+  constexpr uintptr_t bytes = cpl * sizeof(T);
+  static_assert(bytes == 8, "stage kernels copy 8-byte lane vectors (FP32 pairs, FP64 cells)");
+  return nx % cpl == 0 && (uintptr_t)a % bytes == 0 && (uintptr_t)b % bytes == 0;
 }
 
 const char* check_config(const lf_config* c) {
@@ -108,13 +141,9 @@ extern "C" lf_status lf_step_noalloc(const lf_config* cfg, const void* U_in, voi
     lf::set_init_error("lf_step_noalloc: cannot select device %d", cfg->device);
     return LF_ERR_CUDA;
   }
-  lf_status st = LF_OK;
   void* base = nullptr;
-  cudaError_t e = scratch_address(cfg->device, &base);
-  if (e != cudaSuccess) {
-    lf::set_init_error("lf_step_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-    st = LF_ERR_CUDA;
-  } else {
+  lf_status st = scratch_address(cfg->device, static_cast<cudaStream_t>(stream), &base);
+  if (st == LF_OK) {
     lf::MeshDesc m;
     m.nx = cfg->nx;
     m.ny = cfg->ny;
@@ -128,8 +157,9 @@ extern "C" lf_status lf_step_noalloc(const lf_config* cfg, const void* U_in, voi
     m.beta = cfg->limiter == LF_LIMITER_MINMOD ? 1.0 : cfg->beta;
     m.rdx = cfg->nx / (cfg->xmax - cfg->xmin);
     m.rdy = cfg->dim == 2 ? cfg->ny / (cfg->ymax - cfg->ymin) : 0.0;
-    // dense planes: vector access only when every row and plane start stays aligned
-    m.vec = (cfg->nx % 2 == 0) && ((uintptr_t)U_in % 16 == 0) && ((uintptr_t)U_out % 16 == 0);
+    // dense planes (pitch nx): vector access only when every row and plane start stays aligned
+    m.vec = cfg->precision == LF_FP64 ? vector_access_ok<double>(cfg->nx, U_in, U_out)
+                                      : vector_access_ok<float>(cfg->nx, U_in, U_out);
     if (cfg->dim == 2) {  // the tile height of lf_init contexts (or the configured one)
       int sms = 0;
       if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess) sms = 0;
@@ -138,6 +168,7 @@ extern "C" lf_status lf_step_noalloc(const lf_config* cfg, const void* U_in, voi
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     lf::Scalars* sc = static_cast<lf::Scalars*>(base);
     void* ustar = static_cast<unsigned char*>(base) + kScalarBytes;
+    cudaError_t e;
     if (cfg->precision == LF_FP64)
       e = enqueue<double>(m, static_cast<const double*>(U_in), static_cast<double*>(U_out),
                           static_cast<double*>(ustar), sc, dt, cfg->cfl, s);

@@ -83,7 +83,9 @@ SIGNATURES = {
     "lf_profile_read": (ctypes.c_int, [_vp, _P(_d), _P(_i64)]),
     "lf_step_noalloc": (ctypes.c_int, [_P(lf_config), _vp, _vp, _d, _P(_d), _vp]),
     "lf_adjoint_forward": (ctypes.c_int, [_vp, _i32, _P(_d)]),
-    "lf_adjoint_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lf_adjoint_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int]),
+    "lf_adjoint": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _P(_d), ctypes.c_int]),
+    "lf_adjoint_set_passes": (ctypes.c_int, [_vp, _i32]),
     "lf_batch_init": (ctypes.c_int, [_P(lf_config), _i32, _vp, _P(_vp)]),
     "lf_batch_destroy": (None, [_vp]),
     "lf_batch_set_primitive": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, ctypes.c_int]),
@@ -93,6 +95,7 @@ SIGNATURES = {
     "lf_batch_set_rows": (ctypes.c_int, [_vp, _i32]),
     "lf_batch_get_times": (ctypes.c_int, [_vp, _P(_d), _P(_i64)]),
     "lf_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "lf_measure_peak": (ctypes.c_int, [_i32, _i32, _d, _P(_d)]),
     "lf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lf_last_error": (ctypes.c_char_p, [_vp]),
 }
@@ -395,16 +398,43 @@ class LagrangeFlux:
         self._check(_lib.lf_adjoint_forward(self._h, int(nsteps), dts.ctypes.data_as(_P(_d))))
         return dts
 
-    def adjoint_backward(self, lambda_T, grad_U0=None, grad_q0=None):
-        """lambda_T: (4, ny, nx) device tensor dJ/dU(T).  Fills the given device
-        tensors with dJ/dU(0) and/or dJ/d(rho, u, v, p)(0)."""
-        for a in (lambda_T, grad_U0, grad_q0):
+    def _adjoint_buffers(self, bufs):
+        """Pointers and the common side (host/device) of the adjoint buffers,
+        each 4 * nx * ny values of the configured precision."""
+        n = 4 * self.cfg.nx * self.cfg.ny
+        ptrs, kinds = [], set()
+        for a in bufs:
+            p, k = _ptr_and_kind(a)
             if a is not None:
-                if not getattr(a, "is_cuda", False) or not a.is_contiguous():
-                    raise ValueError("adjoint buffers must be contiguous device tensors")
+                if int(np.prod(a.shape)) != n:
+                    raise ValueError(f"adjoint buffer has {int(np.prod(a.shape))} elements, expected {n}")
                 self._check_dtype(a)
-        p = lambda a: None if a is None else a.data_ptr()
-        self._check(_lib.lf_adjoint_backward(self._h, p(lambda_T), p(grad_U0), p(grad_q0)))
+                kinds.add(k)
+            ptrs.append(p)
+        if len(kinds) != 1:
+            raise ValueError("adjoint buffers must all be on the host or all on the device")
+        return ptrs, kinds.pop()
+
+    def adjoint_backward(self, lambda_T, grad_U0=None, grad_q0=None):
+        """lambda_T: (4, ny, nx) dJ/dU(T), a contiguous CUDA tensor or host
+        array.  Fills the given buffers (on the same side) with dJ/dU(0)
+        and/or dJ/d(rho, u, v, p)(0)."""
+        (pl, pu, pq), k = self._adjoint_buffers([lambda_T, grad_U0, grad_q0])
+        self._check(_lib.lf_adjoint_backward(self._h, pl, pu, pq, k))
+
+    def adjoint(self, nsteps: int, lambda_T, grad_U0=None, grad_q0=None) -> np.ndarray:
+        """Forward run of nsteps with checkpoints, then the reverse sweep from
+        the given lambda_T, in one call (lf_adjoint); returns the dt sequence."""
+        (pl, pu, pq), k = self._adjoint_buffers([lambda_T, grad_U0, grad_q0])
+        dts = np.zeros(nsteps)
+        self._check(_lib.lf_adjoint(self._h, int(nsteps), pl, pu, pq, dts.ctypes.data_as(_P(_d)), k))
+        return dts
+
+    ADJOINT_PASSES = {"auto": 0, "tables": 1, "direct": 2}
+
+    def set_adjoint_passes(self, passes: str):
+        """'tables', 'direct' or 'auto' (tables in FP64, direct in FP32)."""
+        self._check(_lib.lf_adjoint_set_passes(self._h, self.ADJOINT_PASSES[passes]))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -503,6 +533,19 @@ class LagrangeFluxBatch:
             self.close()
         except Exception:
             pass
+
+
+PEAK_KINDS = {"fp64": 0, "fp32": 1, "fp32_paired": 2}
+
+
+def measure_peak(kind: str, device: int = 0, target_ms: float = 30.0) -> float:
+    """Measured fused multiply-add throughput (TFLOP/s) of `kind` ('fp64',
+    'fp32' or 'fp32_paired') on `device` (lf_measure_peak)."""
+    r = ctypes.c_double()
+    st = _lib.lf_measure_peak(int(device), PEAK_KINDS[kind], float(target_ms), ctypes.byref(r))
+    if st != LF_OK:
+        raise LagrangeFluxError(st, _lib.lf_last_error(None).decode())
+    return r.value
 
 
 def _autograd_function():

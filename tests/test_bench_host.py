@@ -46,15 +46,18 @@ def test_replicas_take_the_max_time_over_ranks():
 
 
 def test_reference_arm_prints_one_json_line():
+    """The oracle arm on a small mesh of the benchmark's generator; its config
+    names the mesh it ran, and the OpenMP build reports the threads it used."""
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
-                        "--warmup", "1", "--cpu-sample-size", "64"], capture_output=True, text=True, check=True,
+                        "--warmup", "1", "--ref-size", "64"], capture_output=True, text=True, check=True,
                        cwd=ROOT)
     lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
     assert len(lines) == 1
     j = json.loads(lines[0])
     assert j["impl"] == "reference" and j["metric"] == "cell-updates/s" and j["value"] > 0
     assert j["higher_is_better"] is True and j["steps"] == 2 and j["warmup"] == 1
-    assert j["cpu_baseline"]["kind"] == "oracle" and j["cpu_baseline"]["cores"] == 1
+    assert j["cpu_baseline"]["kind"] == "oracle" and j["cpu_baseline"]["cores"] >= 1
+    assert j["config"]["nx"] == 64 and j["config"]["workload"].endswith("64x64")
     assert j["e2e"]["h2d_bytes_per_step"] == 0
 
 

@@ -32,7 +32,7 @@ MUTANTS = {
     "limiter_sign_lost": ("return val(a) > 0.0 ? m : S(-m);", "return m;"),
     "balance_sign": ("acc = acc + A * ahead - A * behind;", "acc = acc + A * behind - A * ahead;"),
     "max_c_is_min": ("S a = max_first(cL, cR);", "S a = min_first(cL, cR);"),
-    "dt_speed_of_one_axis": ("s += (std::fabs(q[1 + d]) + a) / m.h[d];", "s += (std::fabs(q[1]) + a) / m.h[d];"),
+    "dt_speed_of_one_axis": ("s = s + (abs_s(q[1 + d]) + a) / h[d];", "s = s + (abs_s(q[1]) + a) / h[d];"),
     "momentum_pressure_wrong_axis": ("F[1 + dir] = F[1 + dir] + pstar;", "F[1] = F[1] + pstar;"),
     "rk3_stage2_weight": ("U2[l][x] = 0.75 * U[l][x] + 0.25 *", "U2[l][x] = 0.70 * U[l][x] + 0.30 *"),
     "species_fraction_not_divided": ("q[e + 1 + k] = U[e + 1 + k] / rho;", "q[e + 1 + k] = U[e + 1 + k];"),
