@@ -407,11 +407,30 @@ def run_batched(args, dist, dev):
     torch.cuda.synchronize()
     t = dist.max(e0.elapsed_time(e1) / 1e3)
     _, steps = b.times()  # raises on a device error flag
+    # per-stage device time, a separate pass of direct launches bracketed by events
+    pm0, pm1 = b.profile(10)
     b.close()
     cells = sum(nx * ny for nx, ny in sizes)
+    # columns the warp strips compute (64 per strip of 60 outputs in FP32) over the mesh's columns
+    strips = sum(-(-nx // 60) * 64 * ny for nx, ny in sizes)
+    edge = sum((2 if nx > 60 else 1) * 64 * ny for nx, ny in sizes)
+    tile_halo = sum(nx * (ny + 4 * -(-ny // rows)) for nx, ny in sizes)
+    peak, peak_kind = peaks()
+    st = {"stage0": pm0 / 10, "stage1": pm1 / 10}
+    gbs = {k: BYTES_PER_CELL[(k, "fp32")] * cells / (v / 1e3) / 1e9 for k, v in st.items()}
+    dom = max(st, key=st.get)
     return {"value": dist.world * cells * args.batch_steps / t, "unit": METRIC, "problems": len(sizes),
             "cells": cells, "steps": args.batch_steps, "ms_per_step": 1e3 * t / args.batch_steps,
             "tile_rows": rows, "graph": True, "launches_per_step": 4,
+            "stage_ms": [st["stage0"], st["stage1"]],
+            "roofline": {"bound": "hbm", "kernel": "batch_stage_kernel<float, VANLEER, %s>" %
+                         ("predictor" if dom == "stage0" else "corrector"),
+                         "achieved": gbs[dom], "peak": peak, "unit": "GB/s", "frac": gbs[dom] / peak,
+                         "peak_kind": f"{peak_kind} copy bandwidth",
+                         "algorithmic_bytes_per_cell": BYTES_PER_CELL[(dom, "fp32")],
+                         "step_frac": 80 * cells * args.batch_steps / t / 1e9 / peak},
+            "work_shape": {"strip_columns_over_cells": strips / cells, "edge_strip_share": edge / strips,
+                           "rows_read_over_rows": tile_halo / cells},
             "workload": "four-quadrant Riemann problems, sides log-uniform in [64, 1024], seeds 0..P-1"}
 
 

@@ -321,6 +321,13 @@ lf_status lf_batch_set_rows(lf_batch* b, int32_t rows);
  * and returns LF_ERR_NONPHYSICAL if any problem has raised a device error. */
 lf_status lf_batch_get_times(lf_batch* b, double* t, int64_t* steps);
 
+/* Runs nsteps Heun steps of every problem with direct launches (no graph),
+ * each stage launch bracketed by CUDA events on the batch's stream, and
+ * returns in ms[0] / ms[1] the summed device time of the predictor and
+ * corrector launches.  The problems advance as with lf_batch_run.
+ * Synchronises after every step. */
+lf_status lf_batch_profile(lf_batch* b, int32_t nsteps, double ms[2]);
+
 /* Description of the last failure on this batch (NULL: the last failed
  * lf_batch_init). */
 const char* lf_batch_last_error(const lf_batch* b);

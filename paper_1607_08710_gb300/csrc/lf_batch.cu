@@ -483,6 +483,58 @@ lf_status lf_batch_get_times(lf_batch* b, double* t, int64_t* steps) {
   return error_status(b);
 }
 
+lf_status lf_batch_profile(lf_batch* b, int32_t nsteps, double ms[2]) {
+  if (!b || !ms) return LF_ERR_ARG;
+  if (nsteps < 1) {
+    berr(b, "lf_batch_profile: nsteps must be >= 1");
+    return LF_ERR_ARG;
+  }
+  for (int p = 0; p < b->nprob; ++p)
+    if (!b->has_state[p]) {
+      berr(b, "lf_batch_profile: problem %d has no state", p);
+      return LF_ERR_STATE;
+    }
+  Guard g(b->common.device);
+  const lf::BatchDesc d = batch_desc(b);
+  cudaEvent_t ev[4];
+  int made = 0;
+  cudaError_t e = cudaSuccess;
+  for (; made < 4 && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+  if (e != cudaSuccess) made--;
+  float acc[2] = {0.f, 0.f};
+  for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
+    e = lf::launch_batch_begin(b->sc, b->nprob, 0.0, b->counters, b->stream);
+    for (int stage = 0; stage < 2 && e == cudaSuccess; ++stage) {
+      e = cudaEventRecord(ev[2 * stage], b->stream);
+      if (e != cudaSuccess) break;
+      if (b->elem == 8) {
+        double* U = static_cast<double*>(b->U);
+        double* Us = static_cast<double*>(b->Ustar);
+        e = stage == 0 ? lf::launch_batch_stage<double>(0, d, U, U, Us, b->sc, b->counters, b->stream)
+                       : lf::launch_batch_stage<double>(1, d, Us, U, U, b->sc, b->counters + 1, b->stream);
+      } else {
+        float* U = static_cast<float*>(b->U);
+        float* Us = static_cast<float*>(b->Ustar);
+        e = stage == 0 ? lf::launch_batch_stage<float>(0, d, U, U, Us, b->sc, b->counters, b->stream)
+                       : lf::launch_batch_stage<float>(1, d, Us, U, U, b->sc, b->counters + 1, b->stream);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(ev[2 * stage + 1], b->stream);
+    }
+    if (e == cudaSuccess) e = lf::launch_batch_end(b->sc, b->nprob, b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+    for (int stage = 0; stage < 2 && e == cudaSuccess; ++stage) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, ev[2 * stage], ev[2 * stage + 1]);
+      acc[stage] += t;
+    }
+  }
+  for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+  if (e != cudaSuccess) return bcuda(b, e, "lf_batch_profile");
+  ms[0] = acc[0];
+  ms[1] = acc[1];
+  return LF_OK;
+}
+
 const char* lf_batch_last_error(const lf_batch* b) { return b ? b->last_error : lf_last_error(nullptr); }
 
 }  // extern "C"

@@ -25,11 +25,14 @@ batch_stage_kernel(const BatchDesc b, const T* Uin, const T* Un, T* out, Scalars
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* ring = reinterpret_cast<T*>(lf_stage_smem + warp * Ring<T, CPL, 4>::warp_bytes(STAGE));
+  // The counter's answer for the next unit is requested as soon as a unit
+  // starts and read only when the next one starts, so the atomic's round
+  // trip overlaps the current unit's march instead of stalling the warp.
+  int next = lane == 0 ? atomicAdd(counter, 1) : 0;
   for (;;) {
-    int u = 0;
-    if (lane == 0) u = atomicAdd(counter, 1);
-    u = __shfl_sync(FULL, u, 0);
+    const int u = __shfl_sync(FULL, next, 0);
     if (u >= b.nunits) break;
+    if (lane == 0) next = atomicAdd(counter, 1);
     const Unit un = b.units[u];
     const ProbDesc pd = b.probs[un.p];
     Scalars* scp = sc + un.p;

@@ -5,9 +5,10 @@
 // Sec. 5 ride on the same upwind flux as (rho, rho u, rho v, rho E).
 //
 // FP64 uses IEEE division and square root throughout.  FP32 uses the
-// hardware approximate reciprocal and reciprocal square root (__fdividef,
-// rsqrtf): each is within a few ulp, far inside the FP32 error budget of the
-// scheme, and keeps the special-function unit off the critical path.
+// hardware approximate reciprocal and reciprocal square root (the PTX
+// instructions rcp.approx.ftz.f32 and rsqrt.approx.ftz.f32, one
+// special-function instruction each): each is within a few ulp, far inside
+// the FP32 error budget of the scheme; a quotient a / b is a * (1 / b).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -28,14 +29,25 @@ template <> struct Ar<double> {
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 };
 
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 template <> struct Ar<float> {
-  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
-  static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+  static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
+  static __device__ __forceinline__ float div(float a, float b) { return a * rcp_approx(b); }
   static __device__ __forceinline__ void sqrt_and_rsqrt(float x, float& a, float& ia) {
-    ia = rsqrtf(x);
+    ia = rsqrt_approx(x);
     a = x * ia;
   }
-  static __device__ __forceinline__ float sqrt_(float x) { return x * rsqrtf(x); }
+  static __device__ __forceinline__ float sqrt_(float x) { return x * rsqrt_approx(x); }
 };
 
 // Rounding is pinned: the kernels are compiled with -fmad=false, so a
@@ -111,13 +123,13 @@ __device__ __forceinline__ F2 vsel(B2 c, F2 a, F2 b) { return F2(c.x ? a.v.x : b
 __device__ __forceinline__ B2 land(B2 a, B2 b) { return B2{a.x && b.x, a.y && b.y}; }
 
 template <> struct Ar<F2> {
-  static __device__ __forceinline__ F2 rcp(F2 x) { return F2(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.y)); }
+  static __device__ __forceinline__ F2 rcp(F2 x) { return F2(rcp_approx(x.v.x), rcp_approx(x.v.y)); }
   static __device__ __forceinline__ F2 div(F2 a, F2 b) { return a * rcp(b); }
   static __device__ __forceinline__ void sqrt_and_rsqrt(F2 x, F2& a, F2& ia) {
-    ia = F2(rsqrtf(x.v.x), rsqrtf(x.v.y));
+    ia = F2(rsqrt_approx(x.v.x), rsqrt_approx(x.v.y));
     a = x * ia;
   }
-  static __device__ __forceinline__ F2 sqrt_(F2 x) { return x * F2(rsqrtf(x.v.x), rsqrtf(x.v.y)); }
+  static __device__ __forceinline__ F2 sqrt_(F2 x) { return x * F2(rsqrt_approx(x.v.x), rsqrt_approx(x.v.y)); }
 };
 
 // Physics constants of one launch, as lane values.

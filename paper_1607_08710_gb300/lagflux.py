@@ -94,6 +94,7 @@ SIGNATURES = {
     "lf_batch_autotune": (ctypes.c_int, [_vp, _i32, _P(_i32)]),
     "lf_batch_set_rows": (ctypes.c_int, [_vp, _i32]),
     "lf_batch_get_times": (ctypes.c_int, [_vp, _P(_d), _P(_i64)]),
+    "lf_batch_profile": (ctypes.c_int, [_vp, _i32, _P(_d)]),
     "lf_batch_last_error": (ctypes.c_char_p, [_vp]),
     "lf_measure_peak": (ctypes.c_int, [_i32, _i32, _d, _P(_d)]),
     "lf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -522,6 +523,13 @@ class LagrangeFluxBatch:
         s = (ctypes.c_int64 * n)()
         self._check(_lib.lf_batch_get_times(self._h, t, s))
         return np.array(t[:]), np.array(s[:])
+
+    def profile(self, nsteps: int):
+        """nsteps direct-launch steps with per-stage CUDA events; returns the
+        summed (predictor, corrector) device times in ms (lf_batch_profile)."""
+        ms = (ctypes.c_double * 2)()
+        self._check(_lib.lf_batch_profile(self._h, int(nsteps), ms))
+        return ms[0], ms[1]
 
     def close(self):
         if getattr(self, "_h", None):
