@@ -18,14 +18,19 @@
 // warps is computed by both from the same operands in the same order, so the
 // two copies are bitwise equal and the update stays conservative.
 //
-// Memory.  The input planes (the CTA's rows plus halo rows, all fields) are
-// staged into a shared ring four planes deep by cp.async, each warp copying
-// its own row and warps 0-3 one halo row each; the U^n rows of the later
-// stages into a two-plane ring.  CTAs whose strip lies inside the rows make
-// these copies in one CTA-uniform branch, one vector copy per field and row.
-// One commit group per plane: at the top of a step the group issued one step
-// earlier is complete and a barrier makes it visible to the whole CTA.  The
-// planes per z-tile are a launch parameter (Mesh3Desc::tz).
+// Memory.  The CTA's own input rows (all fields) are staged into a shared
+// ring four planes deep by cp.async, each warp copying its own row; the four
+// halo rows, copied by warps 0-3, into a ring two planes deep (they are read
+// only at their own plane); the U^n rows of the later stages into a
+// two-plane ring.  CTAs whose strip lies inside the rows make these copies in
+// one CTA-uniform branch, one vector copy per field and row.  One commit
+// group per plane: at the top of a step the group issued one step earlier is
+// complete.  Every lane reads back only the ring cells it copied, so its own
+// cp.async wait is the only synchronisation the rings need; the warps
+// exchange data only through the primitive plane buffer, which alternates
+// between two buffers from plane to plane, so one barrier per plane (after
+// the buffer is written) suffices.  The planes per z-tile are a launch
+// parameter (Mesh3Desc::tz).
 // Every global index is mapped into the mesh by the boundary condition, and
 // only output cells (column < nx, row < ny, plane < nz) are stored.
 #pragma once
@@ -57,17 +62,23 @@ namespace lf {
 constexpr int ROWS3 = LF_3D_ROWS;  // output rows (warps) per CTA
 constexpr int TZ3 = LF_3D_TZ;      // planes per z-tile
 constexpr int HALO3 = 4;           // y-halo rows, two on each side
-constexpr int RING3 = 4;           // input planes staged (k .. k+3 at step k)
+constexpr int RING3 = 4;           // own input rows: planes staged (k .. k+3 at step k)
+constexpr int HRING3 = 2;          // halo input rows: planes staged (k, k+1 at step k)
 constexpr int RUN3 = 2;            // U^n planes staged (k, k+1 at step k)
 static_assert(ROWS3 >= HALO3, "the halo rows are converted by the first four warps");
 
 template <typename T, int CPL, int NF> struct Smem3 {
   static constexpr int COLS = 32 * CPL;
   static constexpr int ROWSEG = NF * COLS;                   // one row: [field][column]
-  static constexpr int PLANE_IN = (ROWS3 + HALO3) * ROWSEG;  // rows j0-2 .. j0+ROWS3+1
+  static constexpr int PLANE_OWN = ROWS3 * ROWSEG;           // the CTA's rows j0 .. j0+ROWS3-1
+  static constexpr int PLANE_HALO = HALO3 * ROWSEG;          // rows j0-2, j0-1, j0+ROWS3, j0+ROWS3+1
+  static constexpr int PLANE_IN = (ROWS3 + HALO3) * ROWSEG;  // primitives of rows j0-2 .. j0+ROWS3+1
   static constexpr int PLANE_UN = ROWS3 * ROWSEG;            // rows j0 .. j0+ROWS3-1
+  // the own-row ring, the halo-row ring, two primitive plane buffers
+  // (planes alternate between them) and the U^n ring
   static __host__ __device__ constexpr size_t bytes(int stage) {
-    return sizeof(T) * ((size_t)(RING3 + 1) * PLANE_IN + (stage ? (size_t)RUN3 * PLANE_UN : 0));
+    return sizeof(T) * ((size_t)RING3 * PLANE_OWN + (size_t)HRING3 * PLANE_HALO + 2 * (size_t)PLANE_IN +
+                        (stage ? (size_t)RUN3 * PLANE_UN : 0));
   }
 };
 
@@ -121,8 +132,9 @@ struct Args3 {
   const T* Uin;
   const T* Un;
   T* out;
-  T* ring;  // RING3 input planes
-  T* P;     // primitives of the current plane, all CTA rows
+  T* ring;   // RING3 planes of the CTA's own input rows (plane k in slot (k - k0) & 3)
+  T* hring;  // HRING3 planes of the halo input rows (plane k in slot k & 1)
+  T* P;      // primitives of a plane, all CTA rows: two buffers, plane k in buffer k & 1
   T* unr;   // RUN3 U^n planes
   int j0, k0, kend;
   long long own_off;   // element offset of this warp's (mapped) row in a plane of rows
@@ -131,8 +143,8 @@ struct Args3 {
   bool inner;          // the strip lies inside the rows: one vector copy per lane and row (CTA-uniform)
 };
 
-// This warp's copies of input plane `k` into its ring slot: its own row and,
-// for warps 0-3, one halo row, all fields, each lane copying its own CPL cells.
+// This warp's copies of its own row of input plane `k` into the own-row
+// ring, all fields, each lane copying its own CPL cells.
 // AHEAD: k >= 0 (the march's prefetch; the prologue also asks for k0-2, k0-1).
 template <typename T, int STAGE, int CPL, int NF, bool AHEAD = false>
 __device__ __forceinline__ void issue_plane3(const Mesh3Desc& m, const Args3<T, STAGE, NF>& A, const LaneCols<CPL>& L,
@@ -140,28 +152,36 @@ __device__ __forceinline__ void issue_plane3(const Mesh3Desc& m, const Args3<T, 
   using SM = Smem3<T, CPL, NF>;
   const int kz = AHEAD ? map_row_ahead(k, m.nz, m.bc) : map_row(k, m.nz, m.bc);
   const long long zoff = (long long)kz * m.ny * m.pitch;
-  T* slot = A.ring + ((k - A.k0 + 4) & 3) * SM::PLANE_IN + CPL * lane;
+  T* slot = A.ring + ((k - A.k0 + 4) & 3) * SM::PLANE_OWN + warp * SM::ROWSEG + CPL * lane;
   const T* src = A.Uin + zoff + A.own_off;
-  const T* hsrc = A.Uin + zoff + A.halo_off;
-  if (A.inner) {  // a uniform branch around all copies of the plane
+  if (A.inner) {  // a uniform branch around all copies of the row
 #pragma unroll
-    for (int f = 0; f < NF; ++f)
-      cp_async<CPL * sizeof(T)>(slot + (warp + 2) * SM::ROWSEG + f * 32 * CPL, src + f * m.plane + L.c0);
-    if (A.halo_rr >= 0) {
-#pragma unroll
-      for (int f = 0; f < NF; ++f)
-        cp_async<CPL * sizeof(T)>(slot + A.halo_rr * SM::ROWSEG + f * 32 * CPL, hsrc + f * m.plane + L.c0);
-    }
+    for (int f = 0; f < NF; ++f) cp_async<CPL * sizeof(T)>(slot + f * 32 * CPL, src + f * m.plane + L.c0);
     return;
   }
 #pragma unroll
-  for (int f = 0; f < NF; ++f)
-    copy_cells<T, CPL>(slot + (warp + 2) * SM::ROWSEG + f * 32 * CPL, src + f * m.plane, L);
-  if (A.halo_rr >= 0) {
+  for (int f = 0; f < NF; ++f) copy_cells<T, CPL>(slot + f * 32 * CPL, src + f * m.plane, L);
+}
+
+// Warps 0-3: the copies of one halo row of input plane `k` into the
+// halo-row ring (slot k & 1, row index = warp).  The halo rows are used only
+// at their own plane, so they are staged one plane ahead, not three.
+template <typename T, int STAGE, int CPL, int NF, bool AHEAD = false>
+__device__ __forceinline__ void issue_halo3(const Mesh3Desc& m, const Args3<T, STAGE, NF>& A, const LaneCols<CPL>& L,
+                                            int k, int warp, int lane) {
+  using SM = Smem3<T, CPL, NF>;
+  if (A.halo_rr < 0) return;  // uniform over the warp
+  const int kz = AHEAD ? map_row_ahead(k, m.nz, m.bc) : map_row(k, m.nz, m.bc);
+  const long long zoff = (long long)kz * m.ny * m.pitch;
+  T* slot = A.hring + (k & 1) * SM::PLANE_HALO + warp * SM::ROWSEG + CPL * lane;
+  const T* hsrc = A.Uin + zoff + A.halo_off;
+  if (A.inner) {
 #pragma unroll
-    for (int f = 0; f < NF; ++f)
-      copy_cells<T, CPL>(slot + A.halo_rr * SM::ROWSEG + f * 32 * CPL, hsrc + f * m.plane, L);
+    for (int f = 0; f < NF; ++f) cp_async<CPL * sizeof(T)>(slot + f * 32 * CPL, hsrc + f * m.plane + L.c0);
+    return;
   }
+#pragma unroll
+  for (int f = 0; f < NF; ++f) copy_cells<T, CPL>(slot + f * 32 * CPL, hsrc + f * m.plane, L);
 }
 
 // U^n of this warp's own row at plane k (output cells only; plane clamped).
@@ -206,26 +226,33 @@ __device__ __forceinline__ void march_plane3(const Phys<V>& P, const Mesh3Desc& 
                                              int jrow, V ncx, V ncy, V ncz, V rdz, T& smax, bool& bad) {
   using SM = Smem3<T, CPL, NF>;
   constexpr int S1 = (S + 1) % 3, S2 = (S + 2) % 3;
-  // the group issued one step ago (input plane k+2, U^n plane k) has landed
+  // The group issued one step ago (input plane k+2, U^n plane k) has landed.
+  // Every lane reads back only the ring cells it copied itself, so its own
+  // wait suffices there; the one cross-warp exchange, the primitive plane
+  // buffer, alternates between two buffers, so this plane's writes cannot
+  // meet the previous plane's reads (all of them precede the barrier below
+  // in the previous step).
   cp_wait_all();
-  __syncthreads();
-  const T* slot_k = A.ring + ((k - A.k0 + 4) & 3) * SM::PLANE_IN;
+  T* const Pk = A.P + (k & 1) * SM::PLANE_IN;
+  const T* own_k = A.ring + ((k - A.k0 + 4) & 3) * SM::PLANE_OWN + warp * SM::ROWSEG;  // this row, plane k
   {
     V Ut[NF];
-    read_seg<T, CPL, NF>(A.ring + ((k + 2 - A.k0 + 4) & 3) * SM::PLANE_IN + (warp + 2) * SM::ROWSEG, lane, Ut);
+    read_seg<T, CPL, NF>(A.ring + ((k + 2 - A.k0 + 4) & 3) * SM::PLANE_OWN + warp * SM::ROWSEG, lane, Ut);
     to_prim3<V, NF>(P, Ut, M.q[S2]);
   }
   // publish this row's primitives of plane k; warps 0-3 convert the halo rows
-  write_seg<T, CPL, NF>(A.P + (warp + 2) * SM::ROWSEG, lane, M.q[S]);
+  write_seg<T, CPL, NF>(Pk + (warp + 2) * SM::ROWSEG, lane, M.q[S]);
   if (A.halo_rr >= 0) {
     const int rr = A.halo_rr;
     V Uh[NF], qh[NF];
-    read_seg<T, CPL, NF>(slot_k + rr * SM::ROWSEG, lane, Uh);
+    read_seg<T, CPL, NF>(A.hring + (k & 1) * SM::PLANE_HALO + warp * SM::ROWSEG, lane, Uh);
     to_prim3<V, NF>(P, Uh, qh);
-    write_seg<T, CPL, NF>(A.P + rr * SM::ROWSEG, lane, qh);
+    write_seg<T, CPL, NF>(Pk + rr * SM::ROWSEG, lane, qh);
   }
-  // next copies: input plane k+3 (into plane k-1's slot), U^n plane k+1
+  // next copies: own input row of plane k+3 (into plane k-1's slot), halo
+  // row of plane k+1 (into plane k-1's halo slot), U^n plane k+1
   issue_plane3<T, STAGE, CPL, NF, true>(m, A, L, k + 3, warp, lane);
+  issue_halo3<T, STAGE, CPL, NF, true>(m, A, L, k + 1, warp, lane);
   issue_un3<T, STAGE, CPL, NF>(m, A, L, k + 1, warp, lane, jrow);
   cp_commit();
   __syncthreads();
@@ -245,7 +272,7 @@ __device__ __forceinline__ void march_plane3(const Phys<V>& P, const Mesh3Desc& 
   V W[NF];
   {
     V U[NF];
-    read_seg<T, CPL, NF>(slot_k + (warp + 2) * SM::ROWSEG, lane, U);
+    read_seg<T, CPL, NF>(own_k, lane, U);
     if (STAGE >= 1) {
       V Un[NF];
       read_seg<T, CPL, NF>(A.unr + ((k - A.k0) & 1) * SM::PLANE_UN + warp * SM::ROWSEG, lane, Un);
@@ -266,7 +293,7 @@ __device__ __forceinline__ void march_plane3(const Phys<V>& P, const Mesh3Desc& 
   }
   {
     // y: rows j-2 .. j+2 of plane k; slopes at j-1, j, j+1; faces j-1/2, j+1/2
-    const T* P0 = A.P + warp * SM::ROWSEG;  // row j-2
+    const T* P0 = Pk + warp * SM::ROWSEG;  // row j-2
     V Lq[NF], Rq[NF], sj[NF], Glo[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -334,14 +361,21 @@ __device__ __forceinline__ void march_plane3(const Phys<V>& P, const Mesh3Desc& 
   }
 }
 
-// FP32 gas dynamics: LF_3D_MIN_BLOCKS resident CTAs; with species the window
-// carries more fields and the allocator is asked for two; FP64 is uncapped.
-template <typename T, int NF> struct MinBlocks3 { static constexpr int value = NF == 5 ? LF_3D_MIN_BLOCKS : 2; };
-template <int NF> struct MinBlocks3<double, NF> { static constexpr int value = 1; };
+// FP32 gas dynamics: LF_3D_MIN_BLOCKS resident CTAs (LF_3D_MIN_BLOCKS0 for
+// the first stage, whose smaller shared-memory footprint leaves room for
+// more); with species the window carries more fields and the allocator is
+// asked for two; FP64 is uncapped.
+#ifndef LF_3D_MIN_BLOCKS0
+#define LF_3D_MIN_BLOCKS0 LF_3D_MIN_BLOCKS
+#endif
+template <typename T, int STAGE, int NF> struct MinBlocks3 {
+  static constexpr int value = NF == 5 ? (STAGE == 0 ? LF_3D_MIN_BLOCKS0 : LF_3D_MIN_BLOCKS) : 2;
+};
+template <int STAGE, int NF> struct MinBlocks3<double, STAGE, NF> { static constexpr int value = 1; };
 
 // Grid: (strips, ceil(ny / ROWS3), ceil(nz / tz)), tz = m.tz or TZ3; ROWS3 warps per CTA.
 template <typename T, int LIM, int STAGE, int NF>
-__global__ void __launch_bounds__(ROWS3 * 32, (MinBlocks3<T, NF>::value))
+__global__ void __launch_bounds__(ROWS3 * 32, (MinBlocks3<T, STAGE, NF>::value))
 stage3d_kernel(const Mesh3Desc m, const T* __restrict__ Uin, const T* Un, T* out, Scalars* sc) {
   using V = typename StageShape<T>::V;
   constexpr int CPL = StageShape<T>::CPL;
@@ -360,8 +394,9 @@ stage3d_kernel(const Mesh3Desc m, const T* __restrict__ Uin, const T* Un, T* out
   A.Un = Un;
   A.out = out;
   A.ring = reinterpret_cast<T*>(lf_stage3_smem);
-  A.P = A.ring + RING3 * SM::PLANE_IN;
-  A.unr = A.P + SM::PLANE_IN;
+  A.hring = A.ring + RING3 * SM::PLANE_OWN;
+  A.P = A.hring + HRING3 * SM::PLANE_HALO;
+  A.unr = A.P + 2 * SM::PLANE_IN;
   A.j0 = j0;
   const int tz = m.tz > 0 ? m.tz : TZ3;
   A.k0 = blockIdx.z * tz;
@@ -380,6 +415,7 @@ stage3d_kernel(const Mesh3Desc m, const T* __restrict__ Uin, const T* Un, T* out
   // window gets the primitives of planes k0-1 (slot 2), k0 (0), k0+1 (1),
   // the z-slopes of k0-1 and k0 and the flux through face k0-1/2.
   for (int k = k0 - 2; k <= k0 + 1; ++k) issue_plane3<T, STAGE, CPL, NF>(m, A, L, k, warp, lane);
+  issue_halo3<T, STAGE, CPL, NF>(m, A, L, k0, warp, lane);
   issue_un3<T, STAGE, CPL, NF>(m, A, L, k0, warp, lane, jrow);
   cp_commit();
   cp_wait_all();
@@ -390,7 +426,7 @@ stage3d_kernel(const Mesh3Desc m, const T* __restrict__ Uin, const T* Un, T* out
     const int slot_of[4] = {-1, 2, 0, 1};  // register slots of planes k0-1 .. k0+1 (k0-2 goes to qm2)
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      read_seg<T, CPL, NF>(A.ring + ((k0 - 2 + t - k0 + 4) & 3) * SM::PLANE_IN + (warp + 2) * SM::ROWSEG, lane, Ut);
+      read_seg<T, CPL, NF>(A.ring + ((t - 2 + 4) & 3) * SM::PLANE_OWN + warp * SM::ROWSEG, lane, Ut);
       to_prim3<V, NF>(P, Ut, t == 0 ? qm2 : M.q[slot_of[t]]);
     }
     V Lq[NF], Rq[NF];
