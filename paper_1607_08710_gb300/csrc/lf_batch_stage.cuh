@@ -8,15 +8,23 @@
 
 namespace lf {
 
-// Many meshes: a persistent grid whose warps pull work units (problem, strip,
-// row tile) from an atomic counter until the list is exhausted.  Each problem
-// uses its own dt, and its corrector units feed its own wave-speed maximum.
-// (Gas dynamics only: NF = 4.)
+// March code shape of the batched kernel: 1 = one row body with a rotation
+// of the register window, 0 = unrolled by three (as the single-mesh kernel).
+// Persistent warps run unit prologues, inner and edge marches at the same
+// time, so the smaller code matters more here than in the single-mesh grid.
+#ifndef LF_BATCH_ROTATE
+#define LF_BATCH_ROTATE 1
+#endif
 #ifndef LF_BATCH_MIN_BLOCKS
 #define LF_BATCH_MIN_BLOCKS (16 / LF_STAGE_WARPS)
 #endif
 template <typename T> struct BatchMinBlocks { static constexpr int value = LF_BATCH_MIN_BLOCKS; };
 template <> struct BatchMinBlocks<double> { static constexpr int value = 1; };
+
+// Many meshes: a persistent grid whose warps pull work units (problem, strip,
+// row tile) from an atomic counter until the list is exhausted.  Each problem
+// uses its own dt, and its corrector units feed its own wave-speed maximum.
+// (Gas dynamics only: NF = 4.)
 
 template <typename T, int LIM, int STAGE, int CPL>
 __global__ void __launch_bounds__(STAGE_WARPS * 32, (BatchMinBlocks<T>::value))
@@ -55,8 +63,8 @@ batch_stage_kernel(const BatchDesc b, const T* Uin, const T* Un, T* out, Scalars
     // all inner-strip units first, so the warps of an SM run one body at a
     // time (with units in mesh order, alternating bodies measured 18%
     // slower than the mapped body alone, through instruction-cache pressure).
-    strip_tile<T, V, LIM, STAGE, CPL, 4>(P, m, Uin + pd.off, Un + pd.off, out + pd.off, un.i0, un.j0, un.jend, cx, cy,
-                                         ring, lane, smax, bad);
+    strip_tile<T, V, LIM, STAGE, CPL, 4, LF_BATCH_ROTATE != 0>(P, m, Uin + pd.off, Un + pd.off, out + pd.off, un.i0,
+                                                               un.j0, un.jend, cx, cy, ring, lane, smax, bad);
     if (StageCoef<STAGE>::speed) publish_speed(scp, scp->parity ^ 1, smax, bad);
   }
 }

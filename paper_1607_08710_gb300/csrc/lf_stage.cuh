@@ -363,7 +363,7 @@ template <typename T, typename V, int LIM, int STAGE, int CPL, int NF, int S, in
 __device__ __forceinline__ void march_row(const Phys<V>& P, const MeshDesc& m,
                                           const StageArgs<T, STAGE, CPL, NF>& A, const LaneCols<CPL>& L,
                                           March<V, NF>& M, int lane, int r, int si, V ncx, V ncy,
-                                          T& smax, bool& bad) {
+                                          T& smax, bool& bad, int un_cur = S, int un_ahead = (S + 2) % 3) {
   constexpr int S1 = (S + 1) % 3, S2 = (S + 2) % 3;
   constexpr int ROW = Ring<T, CPL, NF>::ROW;
   static_assert(RING_UN == 3, "the U^n ring is indexed by the register slot");
@@ -382,7 +382,8 @@ __device__ __forceinline__ void march_row(const Phys<V>& P, const MeshDesc& m,
   issue_row<T, CPL, NF, MODE>(A.ring_in + ring_in_plus(si, AHEAD_IN) * ROW, A.P, L,
                               map_row_ahead(r + AHEAD_IN, m.ny, m.bc) * m.pitch, lane);
   if (STAGE >= 1)  // U^n row r+2 lives in register slot S2's ring buffer
-    issue_out_cells<T, CPL, NF, MODE>(A.ring_un + S2 * ROW, A.N, L, min(r + AHEAD_UN, m.ny - 1) * m.pitch, lane);
+    issue_out_cells<T, CPL, NF, MODE>(A.ring_un + un_ahead * ROW, A.N, L, min(r + AHEAD_UN, m.ny - 1) * m.pitch,
+                                      lane);
   cp_commit();
   // y-slopes of row r+1 and the flux through face r+1/2
   {
@@ -402,7 +403,7 @@ __device__ __forceinline__ void march_row(const Phys<V>& P, const MeshDesc& m,
   // cells are stored and enter the wave-speed maximum)
   V U[NF], Un[NF];
   read_row<T, CPL, NF>(A.ring_in + si * ROW, lane, U);
-  if (STAGE >= 1) read_row<T, CPL, NF>(A.ring_un + S * ROW, lane, Un);
+  if (STAGE >= 1) read_row<T, CPL, NF>(A.ring_un + un_cur * ROW, lane, Un);
   V W[NF];
 #pragma unroll
   for (int k = 0; k < NF; ++k) {
@@ -441,7 +442,7 @@ __device__ __forceinline__ void march_row(const Phys<V>& P, const MeshDesc& m,
 // [j0, jend): the whole y-march, from the prologue to the last row.  The
 // warp's rings start empty and are left with no copy in flight.
 // STAGE 0: out = Uin - dt L(Uin).  STAGE 1: out = (Un + Uin)/2 - dt/2 L(Uin).
-template <typename T, typename V, int LIM, int STAGE, int CPL, int NF, int MODE>
+template <typename T, typename V, int LIM, int STAGE, int CPL, int NF, int MODE, bool ROT = false>
 __device__ __forceinline__ void strip_tile_impl(const Phys<V>& P, const MeshDesc& m, const T* Uin, const T* Un,
                                                 T* out, int i0, int j0, int jend, T cx, T cy, T* ring_in, int lane,
                                                 T& smax, bool& bad) {
@@ -503,6 +504,27 @@ __device__ __forceinline__ void strip_tile_impl(const Phys<V>& P, const MeshDesc
   // si: input-ring slot of row r (row j0 is in slot 0); the update's dt/dx
   // and dt/dy enter negated (fma(-c, d, b) == fma(c', d, b) with c' = -c)
   const V ncx = V(-cx), ncy = V(-cy);
+  if constexpr (ROT) {
+    // One row body, the register window rotated after each row (a third of
+    // the code of the unrolled march, for a few register moves per row); the
+    // U^n ring follows the row index mod 3.
+    for (int r = j0, si = 0, ui = 0;;) {
+      march_row<T, V, LIM, STAGE, CPL, NF, 0, MODE>(P, m, A, L, M, lane, r, si, ncx, ncy, smax, bad, ui,
+                                                    ui == 0 ? 2 : ui - 1);
+#pragma unroll
+      for (int k = 0; k < NF; ++k) {  // row r+1 -> slot 0, r+2 -> slot 1
+        M.q[0][k] = M.q[1][k];
+        M.q[1][k] = M.q[2][k];
+        M.s[0][k] = M.s[1][k];
+        M.G[0][k] = M.G[1][k];
+      }
+      if (++r >= jend) break;
+      si = ring_in_plus(si, 1);
+      ui = ui == 2 ? 0 : ui + 1;
+    }
+    cp_wait_all();
+    return;
+  }
   for (int r = j0, si = 0;;) {
     march_row<T, V, LIM, STAGE, CPL, NF, 0, MODE>(P, m, A, L, M, lane, r, si, ncx, ncy, smax, bad);
     if (++r >= jend) break;
@@ -521,16 +543,16 @@ __device__ __forceinline__ void strip_tile_impl(const Phys<V>& P, const MeshDesc
 // allowed, runs the march without per-lane copy or store choices (decided
 // once per warp: i0 is warp-uniform); edge strips take the mapped path.  Both
 // do the same arithmetic, so results do not depend on which one ran.
-template <typename T, typename V, int LIM, int STAGE, int CPL, int NF>
+template <typename T, typename V, int LIM, int STAGE, int CPL, int NF, bool ROT = false>
 __device__ __forceinline__ void strip_tile(const Phys<V>& P, const MeshDesc& m, const T* Uin, const T* Un, T* out,
                                            int i0, int j0, int jend, T cx, T cy, T* ring_in, int lane, T& smax,
                                            bool& bad) {
   if (inner_strip<CPL>(m, i0))
-    strip_tile_impl<T, V, LIM, STAGE, CPL, NF, MARCH_INNER>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring_in, lane,
-                                                            smax, bad);
+    strip_tile_impl<T, V, LIM, STAGE, CPL, NF, MARCH_INNER, ROT>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring_in,
+                                                                 lane, smax, bad);
   else
-    strip_tile_impl<T, V, LIM, STAGE, CPL, NF, MARCH_MAPPED>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring_in, lane,
-                                                             smax, bad);
+    strip_tile_impl<T, V, LIM, STAGE, CPL, NF, MARCH_MAPPED, ROT>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring_in,
+                                                                  lane, smax, bad);
 }
 
 // One mesh: a 2D grid of (strips / STAGE_WARPS) x (row tiles) CTAs.
