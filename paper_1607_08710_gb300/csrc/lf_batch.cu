@@ -135,11 +135,16 @@ lf_status build_units(lf_batch* b, int ty) {
     const lf::ProbDesc& d = b->hprobs[p];
     for (int j0 = 0; j0 < d.ny; j0 += ty)
       for (int i0 = 0; i0 < d.nx; i0 += out_cols) {
-        const lf::Unit u{p, i0, j0, std::min(j0 + ty, d.ny)};
+        const lf::Unit u{p, i0, j0, std::min(j0 + ty, d.ny), d};
         if (i0 - 2 >= 0 && i0 - 2 + cols <= d.nx) b->hunits.push_back(u);
         else edge.push_back(u);
       }
   }
+  // Within each group, the short last row tiles of the problems go last, so
+  // that the end of a stage is made of the smallest units.
+  auto taller = [](const lf::Unit& a, const lf::Unit& c) { return a.jend - a.j0 > c.jend - c.j0; };
+  std::stable_sort(b->hunits.begin(), b->hunits.end(), taller);
+  std::stable_sort(edge.begin(), edge.end(), taller);
   b->hunits.insert(b->hunits.end(), edge.begin(), edge.end());
   if (b->hunits.size() > b->units_cap) {
     cudaFree(b->units);

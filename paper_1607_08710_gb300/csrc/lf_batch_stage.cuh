@@ -42,7 +42,7 @@ batch_stage_kernel(const BatchDesc b, const T* Uin, const T* Un, T* out, Scalars
     if (u >= b.nunits) break;
     if (lane == 0) next = atomicAdd(counter, 1);
     const Unit un = b.units[u];
-    const ProbDesc pd = b.probs[un.p];
+    const ProbDesc& pd = un.d;
     Scalars* scp = sc + un.p;
     const double dtd = scp->dt;
     if (!(dtd > 0.0)) continue;  // problem finished (t_end reached) or flagged

@@ -71,9 +71,12 @@ struct ProbDesc {
   long long plane;  // elements between its planes
   double rdx, rdy;
 };
-// A unit of work: one warp strip of one problem over rows [j0, jend).
-struct Unit {
+// A unit of work: one warp strip of one problem over rows [j0, jend), with
+// a copy of the problem's descriptor, so that a warp starting a unit waits
+// for one load of the unit instead of two dependent ones.
+struct alignas(16) Unit {
   int p, i0, j0, jend;
+  ProbDesc d;
 };
 struct BatchDesc {
   MeshDesc common;        // bc, limiter, riemann, gamma, beta, vec (per-problem sizes unused)
