@@ -9,11 +9,12 @@
 namespace lf {
 
 // March code shape of the batched kernel: 1 = one row body with a rotation
-// of the register window, 0 = unrolled by three (as the single-mesh kernel).
+// of the register window, 0 = unrolled by three (as the single-mesh kernel),
+// 2 = the inner march unrolled, the edge-strip march rotating.
 // Persistent warps run unit prologues, inner and edge marches at the same
 // time, so the smaller code matters more here than in the single-mesh grid.
 #ifndef LF_BATCH_ROTATE
-#define LF_BATCH_ROTATE 1
+#define LF_BATCH_ROTATE 2
 #endif
 #ifndef LF_BATCH_MIN_BLOCKS
 #define LF_BATCH_MIN_BLOCKS (16 / LF_STAGE_WARPS)
@@ -63,7 +64,7 @@ batch_stage_kernel(const BatchDesc b, const T* Uin, const T* Un, T* out, Scalars
     // all inner-strip units first, so the warps of an SM run one body at a
     // time (with units in mesh order, alternating bodies measured 18%
     // slower than the mapped body alone, through instruction-cache pressure).
-    strip_tile<T, V, LIM, STAGE, CPL, 4, LF_BATCH_ROTATE != 0>(P, m, Uin + pd.off, Un + pd.off, out + pd.off, un.i0,
+    strip_tile<T, V, LIM, STAGE, CPL, 4, LF_BATCH_ROTATE>(P, m, Uin + pd.off, Un + pd.off, out + pd.off, un.i0,
                                                                un.j0, un.jend, cx, cy, ring, lane, smax, bad);
     if (StageCoef<STAGE>::speed) publish_speed(scp, scp->parity ^ 1, smax, bad);
   }

@@ -543,16 +543,18 @@ __device__ __forceinline__ void strip_tile_impl(const Phys<V>& P, const MeshDesc
 // allowed, runs the march without per-lane copy or store choices (decided
 // once per warp: i0 is warp-uniform); edge strips take the mapped path.  Both
 // do the same arithmetic, so results do not depend on which one ran.
-template <typename T, typename V, int LIM, int STAGE, int CPL, int NF, bool ROT = false>
+// ROT: 0 = both marches unrolled by three, 1 = both with one row body and a
+// rotating register window, 2 = only the mapped (edge-strip) march rotating.
+template <typename T, typename V, int LIM, int STAGE, int CPL, int NF, int ROT = 0>
 __device__ __forceinline__ void strip_tile(const Phys<V>& P, const MeshDesc& m, const T* Uin, const T* Un, T* out,
                                            int i0, int j0, int jend, T cx, T cy, T* ring_in, int lane, T& smax,
                                            bool& bad) {
   if (inner_strip<CPL>(m, i0))
-    strip_tile_impl<T, V, LIM, STAGE, CPL, NF, MARCH_INNER, ROT>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring_in,
-                                                                 lane, smax, bad);
+    strip_tile_impl<T, V, LIM, STAGE, CPL, NF, MARCH_INNER, ROT == 1>(P, m, Uin, Un, out, i0, j0, jend, cx, cy,
+                                                                      ring_in, lane, smax, bad);
   else
-    strip_tile_impl<T, V, LIM, STAGE, CPL, NF, MARCH_MAPPED, ROT>(P, m, Uin, Un, out, i0, j0, jend, cx, cy, ring_in,
-                                                                  lane, smax, bad);
+    strip_tile_impl<T, V, LIM, STAGE, CPL, NF, MARCH_MAPPED, ROT != 0>(P, m, Uin, Un, out, i0, j0, jend, cx, cy,
+                                                                       ring_in, lane, smax, bad);
 }
 
 // One mesh: a 2D grid of (strips / STAGE_WARPS) x (row tiles) CTAs.
