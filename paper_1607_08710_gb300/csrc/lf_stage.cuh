@@ -15,7 +15,9 @@
 // in registers: primitives of three rows, y-slopes and the flux through the
 // face below, each in three slots indexed by row mod 3.  The march is
 // unrolled by three so the slots are compile-time register names and nothing
-// is copied from row to row.  Rows are staged by cp.async into a per-warp
+// is copied from row to row (the batched kernel can instead run one row body
+// and rotate the window after each row: a third of the code, for a few
+// register moves per row).  Rows are staged by cp.async into a per-warp
 // shared-memory ring four rows ahead; the conservative values of the row
 // being updated are read back from the ring rather than carried.  Every
 // primitive, slope and face flux is computed once per cell, up to the 4 halo
