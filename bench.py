@@ -180,7 +180,9 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # helpers
 # ---------------------------------------------------------------------------
-KERNEL_SOURCES = ("lf_device.cuh", "lf_stage.cuh", "lf_internal.h", "lf_kernels_f32.cu", "lf_kernels_f64.cu")
+KERNEL_SOURCES = ("lf_device.cuh", "lf_stage.cuh", "lf_internal.h", "lf_kernels_f32.cu", "lf_kernels_f64.cu",
+                  "lf_device3d.cuh", "lf_stage3d.cuh", "lf_internal3d.h", "lf_kernels3d_f32.cu",
+                  "lf_batch_stage.cuh", "lf_batch.cu")
 
 
 def code_text(src: str) -> str:
@@ -419,13 +421,16 @@ def run_batched(args, dist, dev):
     st = {"stage0": pm0 / 10, "stage1": pm1 / 10}
     gbs = {k: BYTES_PER_CELL[(k, "fp32")] * cells / (v / 1e3) / 1e9 for k, v in st.items()}
     dom = max(st, key=st.get)
+    kb = "batch_stage_kernel<float, VANLEER, %s>" % ("predictor" if dom == "stage0" else "corrector")
+    traffic = measured_traffic(kb, cells)
     return {"value": dist.world * cells * args.batch_steps / t, "unit": METRIC, "problems": len(sizes),
             "cells": cells, "steps": args.batch_steps, "ms_per_step": 1e3 * t / args.batch_steps,
             "tile_rows": rows, "graph": True, "launches_per_step": 4,
             "stage_ms": [st["stage0"], st["stage1"]],
-            "roofline": {"bound": "hbm", "kernel": "batch_stage_kernel<float, VANLEER, %s>" %
-                         ("predictor" if dom == "stage0" else "corrector"),
+            "roofline": {"bound": "hbm", "kernel": kb,
                          "achieved": gbs[dom], "peak": peak, "unit": "GB/s", "frac": gbs[dom] / peak,
+                         "traffic": traffic,
+                         "traffic_frac": None if traffic is None else traffic / (st[dom] / 1e3) / 1e9 / peak,
                          "peak_kind": f"{peak_kind} copy bandwidth",
                          "algorithmic_bytes_per_cell": BYTES_PER_CELL[(dom, "fp32")],
                          "step_frac": 80 * cells * args.batch_steps / t / 1e9 / peak},
@@ -767,12 +772,16 @@ def run_ours(args, dist):
         peak, peak_kind = peaks()
         sk = max(ms, key=ms.get)
         gbs = byts[sk] / (ms[sk] / 1e3) / 1e9
+        k3 = (f"stage3d_kernel<{'float' if prec == 'fp32' else 'double'}, "
+              f"VANLEER, {'predictor' if sk == 'stage0' else 'corrector'}>")
+        traffic3 = measured_traffic(k3, cells3)
         out["3d"] = {
             "value": cells3 * args.steps3d / t3d, "unit": METRIC, "steps": args.steps3d,
             "ms_per_step": 1e3 * t3d / args.steps3d, "stage_ms": [ms["stage0"], ms["stage1"]],
-            "roofline": {"bound": "hbm", "kernel": f"stage3d_kernel<{'float' if prec == 'fp32' else 'double'}, "
-                         f"VANLEER, {'predictor' if sk == 'stage0' else 'corrector'}>",
+            "roofline": {"bound": "hbm", "kernel": k3,
                          "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "traffic": traffic3,
+                         "traffic_frac": None if traffic3 is None else traffic3 / (ms[sk] / 1e3) / 1e9 / peak,
                          "peak_kind": f"{peak_kind} copy bandwidth",
                          "algorithmic_bytes_per_cell": byts[sk] // cells3},
             "workload": f"periodic 3D shear layer {n3}^3 (Kelvin-Helmholtz layer, perturbation x cos(2 pi z))"}
