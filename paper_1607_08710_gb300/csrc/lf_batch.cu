@@ -120,15 +120,23 @@ lf::MeshDesc problem_mesh(const lf_batch* b, int p) {
   return m;
 }
 
+// Order of the unit list: 1 = mesh order (problem by problem, row tile by row
+// tile, strip by strip: neighbouring units share halo rows and columns while
+// they are in L2); 0 = the inner-strip units of all problems, then the
+// edge-strip units (measured as fast only while the two march bodies were
+// unrolled and competed for the instruction cache).  Either way the short
+// last row tiles go to the end.
+#ifndef LF_BATCH_ORDER
+#define LF_BATCH_ORDER 1
+#endif
+
 // Work units for a tile height: problem by problem, row tile by row tile,
 // strip by strip, so that warps taking consecutive units share halo rows.
 lf_status build_units(lf_batch* b, int ty) {
   const int cols = b->elem == 4 ? 64 : 32;  // columns of a warp strip (CPL=2 FP32, CPL=1 FP64)
   const int out_cols = cols - 4;           // its output columns
-  // Units of strips that lie inside their rows (the kernel's inner march)
-  // first, then the edge strips (the mapped march): warps take units in list
-  // order, so an SM runs mostly one of the two march bodies at a time instead
-  // of alternating between them (instruction-cache pressure).
+  // (LF_BATCH_ORDER 0: units of strips that lie inside their rows -- the
+  // kernel's inner march -- first, then the edge strips on the mapped march.)
   b->hunits.clear();
   std::vector<lf::Unit> edge;
   for (int p = 0; p < b->nprob; ++p) {
@@ -136,7 +144,7 @@ lf_status build_units(lf_batch* b, int ty) {
     for (int j0 = 0; j0 < d.ny; j0 += ty)
       for (int i0 = 0; i0 < d.nx; i0 += out_cols) {
         const lf::Unit u{p, i0, j0, std::min(j0 + ty, d.ny), d};
-        if (i0 - 2 >= 0 && i0 - 2 + cols <= d.nx) b->hunits.push_back(u);
+        if (LF_BATCH_ORDER == 1 || (i0 - 2 >= 0 && i0 - 2 + cols <= d.nx)) b->hunits.push_back(u);
         else edge.push_back(u);
       }
   }

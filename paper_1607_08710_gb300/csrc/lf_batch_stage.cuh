@@ -14,7 +14,7 @@ namespace lf {
 // Persistent warps run unit prologues, inner and edge marches at the same
 // time, so the smaller code matters more here than in the single-mesh grid.
 #ifndef LF_BATCH_ROTATE
-#define LF_BATCH_ROTATE 2
+#define LF_BATCH_ROTATE 1
 #endif
 #ifndef LF_BATCH_MIN_BLOCKS
 #define LF_BATCH_MIN_BLOCKS (16 / LF_STAGE_WARPS)
@@ -60,10 +60,10 @@ batch_stage_kernel(const BatchDesc b, const T* Uin, const T* Un, T* out, Scalars
     const T cx = T(hs * dtd * m.rdx), cy = T(hs * dtd * m.rdy);
     T smax = T(0);
     bool bad = false;
-    // The inner or the mapped march, as for one mesh.  The unit list puts
-    // all inner-strip units first, so the warps of an SM run one body at a
-    // time (with units in mesh order, alternating bodies measured 18%
-    // slower than the mapped body alone, through instruction-cache pressure).
+    // The inner or the mapped march, as for one mesh.  (With both marches
+    // unrolled by three and the units in mesh order, the alternating bodies
+    // measured 18% slower than the mapped body alone, through instruction-cache
+    // pressure; with the rotating marches, mesh order is the faster order.)
     strip_tile<T, V, LIM, STAGE, CPL, 4, LF_BATCH_ROTATE>(P, m, Uin + pd.off, Un + pd.off, out + pd.off, un.i0,
                                                                un.j0, un.jend, cx, cy, ring, lane, smax, bad);
     if (StageCoef<STAGE>::speed) publish_speed(scp, scp->parity ^ 1, smax, bad);
