@@ -26,7 +26,6 @@ struct lf_batch {
   void* Ustar = nullptr;            // pool of predictor states
   size_t pool_elems = 0;
   std::vector<lf::ProbDesc> hprobs;
-  lf::ProbDesc* probs = nullptr;
   std::vector<lf::Unit> hunits;
   lf::Unit* units = nullptr;
   size_t units_cap = 0;
@@ -175,7 +174,6 @@ lf_status build_units(lf_batch* b, int ty) {
 lf::BatchDesc batch_desc(const lf_batch* b) {
   lf::BatchDesc d;
   d.common = problem_mesh(b, 0);
-  d.probs = b->probs;
   d.units = b->units;
   d.nunits = (int)b->hunits.size();
   d.grid = b->grid;
@@ -266,13 +264,10 @@ lf_status lf_batch_init(const lf_config* cfgs, int32_t nprob, void* stream, lf_b
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc(&b->U, off * b->elem);
   if (e == cudaSuccess) e = cudaMalloc(&b->Ustar, off * b->elem);
-  if (e == cudaSuccess) e = cudaMalloc(&b->probs, nprob * sizeof(lf::ProbDesc));
   if (e == cudaSuccess) e = cudaMalloc(&b->sc, nprob * sizeof(lf::Scalars));
   if (e == cudaSuccess) e = cudaMalloc(&b->counters, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&b->hsc, nprob * sizeof(lf::Scalars));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->probs, b->hprobs.data(), nprob * sizeof(lf::ProbDesc), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->U, 0, off * b->elem, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->Ustar, 0, off * b->elem, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->counters, 0, 2 * sizeof(int), b->stream);
@@ -307,7 +302,6 @@ void lf_batch_destroy(lf_batch* b) {
     if (b->capture) cudaStreamDestroy(b->capture);
     cudaFree(b->U);
     cudaFree(b->Ustar);
-    cudaFree(b->probs);
     cudaFree(b->units);
     cudaFree(b->sc);
     cudaFree(b->counters);

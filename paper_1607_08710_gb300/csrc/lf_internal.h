@@ -80,7 +80,6 @@ struct alignas(16) Unit {
 };
 struct BatchDesc {
   MeshDesc common;        // bc, limiter, riemann, gamma, beta, vec (per-problem sizes unused)
-  const ProbDesc* probs;  // device
   const Unit* units;      // device
   int nunits;
   int grid;               // persistent CTAs
