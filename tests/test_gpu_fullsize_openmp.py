@@ -1,6 +1,7 @@
 """The benchmark's full workloads -- the 8192^2 periodic Kelvin-Helmholtz layer
 (ten CFL steps), the 384^3 periodic 3D shear layer (five) and the 512 batched
-four-quadrant problems (ten) -- on the GPU, against the FP64 oracle run on the
+four-quadrant problems (ten) -- and the 2048^2 four-quadrant problem of the
+FP64/FP32 configuration (its 400 steps) on the GPU, against the FP64 oracle run on the
 whole meshes on the host's cores (the OpenMP build for the single meshes, the
 same bits as the plain build, test_oracle_openmp.py; the plain build in a
 pool of processes, one problem each, for the batch): every cell of every field
@@ -164,3 +165,38 @@ def test_whole_512_problem_batch_ten_steps_against_oracle(batch_reference, preci
             worst = max(worst, err)
             assert err <= tol, f"{precision} problem {p} {sizes[p]} field {field}: relative L1 {err:.3e} > {tol}"
     print(f"512 batched problems {precision}: worst relative L1 over problems and fields {worst:.3e}")
+
+
+N1, STEPS1 = 2048, 400
+KW_1 = dict(limiter="vanleer", bc="transmissive", cfl=0.45)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_2048_quadrant_400_steps_against_openmp_oracle(precision):
+    """2048^2 cells on [0,1]^2, seeded four-quadrant Riemann problem, van Leer,
+    CFL 0.45, transmissive boundaries, 400 steps: FP64 with the oracle's own CFL
+    dt sequence, FP32 on the GPU's."""
+    tdt = torch.float64 if precision == "fp64" else torch.float32
+    prim = inputs.quadrant(N1, N1, seed=0).stack()
+    s = LagrangeFlux(Config(nx=N1, ny=N1, precision=precision, **KW_1))
+    q = torch.from_numpy(prim).to("cuda", tdt)
+    s.set_primitive(q[0], q[1], q[2], q[3])
+    U = torch.empty((4, N1, N1), dtype=tdt, device="cuda")
+    s.get_state(U)
+    U0 = U.double().cpu().numpy()
+    dts = [s.step(return_dt=True) for _ in range(STEPS1)]
+    s.get_state(U)
+    got = U.double().cpu().numpy()
+    s.close()
+    oc = O.OracleConfig(nx=N1, ny=N1, **KW_1)
+    with O.use_library(O.build_omp()):
+        O.threads(host_cores())
+        ref = O.run(oc, U0, STEPS1) if precision == "fp64" else O.run(oc, U0, STEPS1, dts=dts)
+    assert ref.steps == STEPS1
+    if precision == "fp64":
+        np.testing.assert_allclose(dts, ref.dts, rtol=1e-13, atol=0)
+    tol = 1e-12 if precision == "fp64" else 2e-5
+    for field in range(4):
+        err = np.abs(got[field] - ref.U[field]).sum() / np.abs(ref.U[field]).sum()
+        print(f"2048^2 quadrant {precision} field {field}: relative L1 {err:.3e}")
+        assert err <= tol, f"{precision} field {field}: relative L1 {err:.3e} > {tol}"
